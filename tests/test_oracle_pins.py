@@ -1,0 +1,311 @@
+"""Pins for the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: hand-derived
+values, closed forms, invariants, brute force on tiny inputs, or a textbook
+special case.  Paper references: Section I (one particle per leaf, centre of
+mass per cube), Section III and Fig. 1 (opening criterion), Fig. 2 (worked
+example).  No GPU needed.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _pm(points, masses=None):
+    p = np.asarray(points, dtype=np.float64)
+    n = p.shape[0]
+    pm = np.zeros((n, 4))
+    pm[:, :p.shape[1]] = p
+    pm[:, 3] = 1.0 / n if masses is None else masses
+    return pm
+
+
+# ----------------------------------------------------------------- summation
+
+def test_neumaier_compensation_survives_compilation(oracle_lib):
+    # Naive left-to-right summation returns 0 and 0 for these; the exact sums are 1 and 2.
+    assert oracle.nsum([1e16, 1.0, -1e16]) == 1.0
+    assert oracle.nsum([1.0, 1e100, 1.0, -1e100]) == 2.0
+
+
+# ---------------------------------------------------------------------- keys
+
+def test_keys_hand_derived(oracle_lib):
+    with open(os.path.join(GOLDEN, "keys_hand.json")) as f:
+        cases = json.load(f)["cases"]
+    for case in cases:
+        k = oracle.keys(_pm(case["points"]))
+        assert [int(x) for x in k] == [int(x) for x in case["keys"]], case["name"]
+
+
+def test_key_octant_matches_geometry(oracle_lib):
+    # Level-1 octant = 4*[x in upper half] + 2*[y upper] + [z upper] (x most significant).
+    rng = np.random.default_rng(7)
+    p = rng.uniform(-3, 5, (500, 3))
+    pm = _pm(np.vstack([p, [[-3, -3, -3], [5, 5, 5]]]))  # pin the cube to [-3, 5]^3
+    k = oracle.keys(pm)
+    oct1 = (k >> np.uint64(60)).astype(int)
+    mid = 1.0
+    want = 4 * (pm[:, 0] >= mid) + 2 * (pm[:, 1] >= mid) + (pm[:, 2] >= mid)
+    far = np.all(np.abs(pm[:, :3] - mid) > 1e-5, axis=1)
+    assert np.array_equal(oct1[far], want[far])
+
+
+def test_key_rule_rounds_in_single_precision(oracle_lib):
+    # The rule quantises with FP32 round-to-nearest operations.  numpy float32
+    # arithmetic is an independent IEEE implementation of the same operations;
+    # we look for points where exact (FP64) arithmetic would give another
+    # integer and check the oracle follows the FP32 rule there.
+    rng = np.random.default_rng(11)
+    x = rng.uniform(-1, 1, 200000).astype(np.float32)
+    lo = np.float32(-1.0)
+    side = np.float32(2.0)
+    scale = np.float32(2097152.0) / side
+    q32 = np.floor((x - lo) * scale).astype(np.int64)
+    q64 = np.floor((x.astype(np.float64) + 1.0) * 2097152.0 / 2.0).astype(np.int64)
+    differ = np.nonzero(q32 != q64)[0]
+    assert differ.size > 0
+    pts = np.zeros((differ.size + 2, 3))
+    pts[:-2, 0] = x[differ]
+    pts[-2] = [-1, -1, -1]
+    pts[-1] = [1, 1, 1]
+    k = oracle.keys(_pm(pts))[:-2]
+    # de-interleave qx from the key
+    qx = np.zeros(k.size, np.int64)
+    for b in range(21):
+        qx |= ((k >> np.uint64(3 * b + 2)) & np.uint64(1)).astype(np.int64) << b
+    assert np.array_equal(qx, np.clip(q32[differ], 0, 2 ** 21 - 1))
+
+
+# ------------------------------------------------------------------ topology
+
+def _brute_force_nodes(pm):
+    """Every (level, prefix) cell by enumeration: a cell is a node iff it is the
+    root or its parent cell holds >= 2 particles (and the parent is above the
+    depth cap); sorted into depth-first Morton order."""
+    k = oracle.keys(pm)
+    n = len(k)
+    order = np.lexsort((np.arange(n), k))  # key, then input index
+    ks = k[order]
+    nodes = []
+    for lvl in range(22):
+        pref = ks >> np.uint64(3 * (21 - lvl))
+        parent = ks >> np.uint64(3 * (21 - lvl + 1)) if lvl > 0 else None
+        starts = [0] + [i for i in range(1, n) if pref[i] != pref[i - 1]]
+        for a, s in enumerate(starts):
+            e = starts[a + 1] if a + 1 < len(starts) else n
+            if lvl > 0:
+                pc = np.count_nonzero(parent == parent[s])
+                if pc < 2:
+                    continue
+            nodes.append((int(pref[s]) << (3 * (21 - lvl)), lvl, int(pref[s]), s, e - s))
+    nodes.sort()
+    out = []
+    for i, (_, lvl, pre, first, cnt) in enumerate(nodes):
+        cm = 0
+        if cnt > 1 and lvl < 21:
+            for (_, l2, p2, f2, c2) in nodes:
+                if l2 == lvl + 1 and (p2 >> 3) == pre:
+                    cm |= 1 << (p2 & 7)
+        out.append((lvl, pre, first, cnt, cm))
+    return out, order
+
+
+@pytest.mark.parametrize("kind,n,seed", [
+    ("gauss", 1, 1), ("gauss", 2, 2), ("gauss", 17, 3), ("planar", 33, 4),
+    ("clustered", 48, 5), ("line", 40, 6), ("gauss", 64, 7), ("dups", 30, 8),
+])
+def test_topology_recursive_insertion_equals_enumeration(oracle_lib, kind, n, seed):
+    if kind == "dups":
+        pm, _ = synth.random_cloud(n, seed, "gauss")
+        pm = pm.astype(np.float64)
+        pm[5:12, :3] = pm[3, :3]      # a bucket of 8 coincident points
+        pm[20:23, :3] = pm[19, :3]
+    else:
+        pm, _ = synth.random_cloud(n, seed, kind)
+    T = oracle.Tree(pm)
+    nd = T.nodes()
+    got = list(zip(nd["level"].tolist(), nd["prefix"].tolist(), nd["first"].tolist(),
+                   nd["count"].tolist(), nd["childmask"].tolist()))
+    want, order = _brute_force_nodes(pm.astype(np.float64))
+    assert got == want
+    o, _ = T.order()
+    assert np.array_equal(o, order)
+
+
+def test_topology_hand_cases(oracle_lib):
+    with open(os.path.join(GOLDEN, "topology_hand.json")) as f:
+        cases = json.load(f)["cases"]
+    for case in cases:
+        T = oracle.Tree(_pm(case["points"]))
+        nd = T.nodes()
+        got = [[int(nd["level"][i]), int(nd["prefix"][i]), int(nd["first"][i]),
+                int(nd["count"][i]), int(nd["childmask"][i])] for i in range(T.m)]
+        assert got == case["nodes"], case["name"]
+        o, _ = T.order()
+        assert o.tolist() == case["order"], case["name"]
+
+
+# ----------------------------------------------------------- centre of mass
+
+def test_com_invariants(oracle_lib):
+    pm, _ = synth.random_cloud(3000, 21, "clustered")
+    pm = pm.astype(np.float64)
+    T = oracle.Tree(pm)
+    nd = T.nodes()
+    o, _ = T.order()
+    m = pm[o, 3]
+    x = pm[o, :3]
+    # root: total mass and mass-weighted mean
+    assert nd["level"][0] == 0
+    assert abs(nd["mass"][0] - m.sum()) <= 1e-14 * m.sum()
+    np.testing.assert_allclose(nd["com"][0], (m[:, None] * x).sum(0) / m.sum(), rtol=0,
+                               atol=1e-14 * np.abs(x).max())
+    # every node: mass and centre of its member particles
+    cs = np.concatenate([[0.0], np.cumsum(m)])
+    for i in range(T.m):
+        f, c = nd["first"][i], nd["count"][i]
+        mm = m[f:f + c].sum()
+        assert abs(nd["mass"][i] - mm) <= 1e-13 * mm
+        com = (m[f:f + c, None] * x[f:f + c]).sum(0) / mm
+        np.testing.assert_allclose(nd["com"][i], com, rtol=0, atol=1e-12 * (1 + np.abs(com).max()))
+
+
+# ---------------------------------------------------------------------- force
+
+def test_direct_sum_two_body_closed_form(oracle_lib):
+    # |a_1| = G m_2 / r^2 exactly, pointing at body 2 (eps = 0).
+    pm = _pm([[0.3, -0.2, 0.1], [1.3, 0.8, -0.4]], [2.0, 0.5])
+    acc, pot = oracle.direct(pm, eps=0.0, G=1.7)
+    r = np.array([1.0, 1.0, -0.5])
+    rr = np.linalg.norm(r)
+    np.testing.assert_allclose(acc[0], 1.7 * 0.5 * r / rr ** 3, rtol=1e-15)
+    np.testing.assert_allclose(acc[1], -1.7 * 2.0 * r / rr ** 3, rtol=1e-15)
+    np.testing.assert_allclose(pot, [-1.7 * 0.5 / rr, -1.7 * 2.0 / rr], rtol=1e-15)
+
+
+def test_direct_sum_cube_vertices_closed_form(oracle_lib):
+    # 8 unit masses on the vertices of [-1,1]^3.  The pull on (1,1,1) points
+    # along -(1,1,1)/sqrt3 with magnitude 3/(4 sqrt3) + (3/8) sqrt(2/3) + 1/12
+    # (three edge neighbours at 2, three face diagonals at 2 sqrt2, one body
+    # diagonal at 2 sqrt3), derived by hand.
+    v = np.array([[x, y, z] for x in (-1, 1) for y in (-1, 1) for z in (-1, 1)], float)
+    acc, pot = oracle.direct(_pm(v, np.ones(8)), eps=0.0)
+    mag = 3 / (4 * math.sqrt(3)) + (3 / 8) * math.sqrt(2 / 3) + 1 / 12
+    i = 7  # (1,1,1)
+    np.testing.assert_allclose(acc[i], -mag / math.sqrt(3) * np.ones(3), rtol=1e-14)
+    np.testing.assert_allclose(pot[i], -(3 / 2 + 3 / (2 * math.sqrt(2)) + 1 / (2 * math.sqrt(3))),
+                               rtol=1e-14)
+
+
+def test_theta_zero_is_direct_summation(oracle_lib):
+    # theta = 0 never accepts a cell, so the walk is the direct sum; the gate is
+    # max_i |a_tree - a_direct| / sum_j |G m_j r_ij|/(r^2+eps^2)^(3/2) <= 1e-12.
+    pm, _ = synth.plummer(1500, 1)
+    pm = pm.astype(np.float64)
+    eps = 0.01
+    at, pt, cnt = oracle.Tree(pm).accel(0.0, eps)
+    ad, pd = oracle.direct(pm, eps)
+    x, m = pm[:, :3], pm[:, 3]
+    r = x[None, :, :] - x[:, None, :]
+    r2 = (r ** 2).sum(-1) + eps ** 2
+    scale = (m[None, :] * np.sqrt((r ** 2).sum(-1)) / r2 ** 1.5).sum(1)
+    assert (np.abs(at - ad).max(1) / scale).max() <= 1e-12
+    assert np.all(cnt == len(pm))  # every particle individually
+
+
+def test_momentum_conserved_by_pairwise_sums(oracle_lib):
+    pm, _ = synth.random_cloud(700, 3, "gauss")
+    pm = pm.astype(np.float64)
+    m = pm[:, 3]
+    for acc in (oracle.direct(pm, 0.05)[0], oracle.Tree(pm).accel(0.0, 0.05)[0]):
+        tot = (m[:, None] * acc).sum(0)
+        assert np.abs(tot).max() <= 1e-13 * (m[:, None] * np.abs(acc)).sum()
+
+
+def test_error_decreases_as_theta_decreases(oracle_lib):
+    pm, _ = synth.plummer(3000, 2)
+    pm = pm.astype(np.float64)
+    ad, _ = oracle.direct(pm, 0.01)
+    T = oracle.Tree(pm)
+    errs = []
+    for th in (1.0, 0.7, 0.5, 0.3, 0.15):
+        a, _, _ = T.accel(th, 0.01)
+        errs.append(np.median(np.linalg.norm(a - ad, axis=1) / np.linalg.norm(ad, axis=1)))
+    assert all(e1 > e2 for e1, e2 in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-4
+
+
+def test_fig2_two_inputs_for_remote_particles(oracle_lib):
+    # Fig. 2 (Section III): four particles in a 2-D domain; P3 and P4 cluster in
+    # node N2, so P1 and P2 each need only two inputs (the other remote
+    # particle and N2's centroid).  Counts below exclude the self term.
+    with open(os.path.join(GOLDEN, "fig2_shape.json")) as f:
+        g = json.load(f)
+    pm = _pm(g["points"])
+    _, _, cnt = oracle.Tree(pm).accel(g["theta"], g["eps"])
+    assert (cnt - 1).tolist() == g["inputs_excluding_self"]
+
+
+# --------------------------------------------------------------- integrator
+
+def test_leapfrog_kepler_orbit_second_order(oracle_lib):
+    pm, vel, k = synth.kepler_pair(0.6, 0.4, 1.0, 0.5)
+    x0 = pm.astype(np.float64)
+    T = k["period"]
+    errs = []
+    for nsteps in (500, 1000, 2000):
+        p, v, _ = oracle.leapfrog(x0, vel, nsteps, T / nsteps, theta=0.5, eps=0.0)
+        errs.append(np.abs(p[:, :3] - x0[:, :3]).max())
+    # KDK is second order: halving dt divides the one-orbit error by ~4.
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0, errs
+    assert errs[-1] < 1e-3
+
+
+def test_leapfrog_kepler_energy_and_reversibility(oracle_lib):
+    pm, vel, k = synth.kepler_pair(0.6, 0.4, 1.0, 0.5)
+    x0 = pm.astype(np.float64)
+    dt = k["period"] / 1000
+    p, v, a = oracle.leapfrog(x0, vel, 1000, dt, theta=0.5, eps=0.0)
+    e0 = 0.5 * 0.6 * (vel[0, :3].astype(float) ** 2).sum() + 0.5 * 0.4 * (vel[1, :3].astype(float) ** 2).sum() \
+        - 0.6 * 0.4 / k["rp"]
+    e1 = 0.5 * 0.6 * (v[0] ** 2).sum() + 0.5 * 0.4 * (v[1] ** 2).sum() \
+        - 0.6 * 0.4 / np.linalg.norm(p[0, :3] - p[1, :3])
+    assert abs(e1 - e0) < 1e-4 * abs(e0)
+    # run backwards: the scheme is time-reversible
+    pb, vb, _ = oracle.leapfrog(p, -v, 1000, dt, theta=0.5, eps=0.0, acc=a)
+    np.testing.assert_allclose(pb[:, :3], x0[:, :3], atol=1e-10)
+
+
+def test_diagnostics_hand_values(oracle_lib):
+    pm = _pm([[1.0, 0, 0], [-1.0, 0, 0], [0, 2.0, 0]], [1.0, 2.0, 3.0])
+    vel = np.array([[0, 1.0, 0], [0, 0, 2.0], [3.0, 0, 0]])
+    phi = np.array([-1.0, -2.0, -3.0])
+    d = oracle.diagnostics(pm, vel, phi)
+    # KE = 0.5(1*1 + 2*4 + 3*9) = 18; PE = 0.5(-1 - 4 - 9) = -7
+    # P = (9, 1, 4); COM = (1 - 2 + 0, 6, 0)/6
+    np.testing.assert_allclose(d, [18.0, -7.0, 9.0, 1.0, 4.0, -1 / 6, 1.0, 0.0], rtol=1e-15)
+
+
+# ----------------------------------------------------------- input recipe
+
+def test_plummer_generator_matches_model(oracle_lib):
+    # Half-mass radius of the a=1 Plummer sphere is (2^(2/3) - 1)^(-1/2) = 1.3048;
+    # virial equilibrium: 2 KE + PE = 0 with KE = 3 pi/64, PE = -3 pi/32 (G=M=a=1).
+    pm, vel = synth.plummer(100000, 9)
+    r = np.sort(np.linalg.norm(pm[:, :3].astype(np.float64), axis=1))
+    assert abs(r[len(r) // 2] - 1.3048) < 0.03
+    assert abs(pm[:, 3].astype(np.float64).sum() - 1.0) < 1e-5
+    pm2, vel2 = synth.plummer(4096, 10)
+    _, pot = oracle.direct(pm2, 1e-4)
+    d = oracle.diagnostics(pm2, vel2, pot)
+    assert abs(d[0] - 3 * math.pi / 64) < 0.1 * 3 * math.pi / 64
+    assert abs(2 * d[0] + d[1]) < 0.1 * abs(d[1])

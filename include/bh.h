@@ -1,0 +1,303 @@
+/*
+ * bh.h -- C ABI of the GB300 Barnes-Hut library (libbh.so).
+ *
+ * The library computes the data-parallel hot path of the Barnes-Hut method as
+ * studied in Dekate et al., "Improving the scalability of parallel N-body
+ * applications with an event driven constraint based execution model"
+ * (arXiv:1109.5190):
+ *   - Section I: n particles evolve under pairwise gravitational forces; the
+ *     particles are grouped in a hierarchy of cubes subdivided until each
+ *     holds one particle, and a centre of mass is kept per cube.
+ *   - Section III, Fig. 1: a remote cluster is replaced by a single body when
+ *     it is far enough away relative to its size, theta setting the error.
+ *   - Section III: a global barrier at tree construction in every iteration,
+ *     then the force computation, the most expensive stage.
+ * What the paper leaves unstated is fixed as follows (the same readings as
+ * the test oracle): Plummer-softened Newtonian forces; the opening test
+ * s^2 < theta^2 d^2 with s = side / 2^level and d the distance to the cell's
+ * centre of mass, leaves taken particle by particle; 63-bit Morton keys from a
+ * 21-bit FP32 quantisation of the bounding cube; a depth cap of 21 levels,
+ * where coincident points share one leaf; kick-drift-kick leapfrog.
+ *
+ * Conventions for every call:
+ *   - Return value: BH_OK (0) on success, BH_PENDING (1) from bh_poll when a
+ *     result is not ready, a negative BH_ERR_* code otherwise.  Nothing traps
+ *     on the device; device-side failures (node capacity, bounded waits) come
+ *     back as status codes.  bh_last_error() returns a message for the last
+ *     failing call on the calling thread.
+ *   - Particle arrays are float32, 4 values per particle: pos_mass = (x, y, z,
+ *     m), vel = (vx, vy, vz, unused), acc = (ax, ay, az, phi).  They are in
+ *     the caller's particle order (particle i is row i) for input and output.
+ *   - Pointers are host pointers unless the call's flags include
+ *     BH_DEVICE_PTRS, in which case they are device pointers readable or
+ *     writable on the system's stream during the call only.  The caller keeps
+ *     ownership of every array it passes; the library copies what it keeps.
+ *   - Every call that returns BH_OK has finished its device work (the stream
+ *     is synchronised) unless its comment says otherwise.
+ *   - Handles are not thread-safe: one thread at a time per handle.  A
+ *     bh_server handle may be used from any thread.
+ */
+#ifndef BH_H
+#define BH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define BH_OK             0
+#define BH_PENDING        1
+#define BH_ERR_INVALID   (-1)  /* bad argument (size, pointer, parameter value) */
+#define BH_ERR_OOM       (-2)  /* device or host allocation failed */
+#define BH_ERR_BUDGET    (-3)  /* request larger than the server's HBM budget */
+#define BH_ERR_CAPACITY  (-4)  /* node buffer overflow that could not be recovered */
+#define BH_ERR_TIMEOUT   (-5)  /* a bounded wait expired */
+#define BH_ERR_CUDA      (-6)  /* a CUDA runtime call failed */
+#define BH_ERR_STATE     (-7)  /* call not valid in the handle's current state */
+#define BH_ERR_CANCELLED (-8)  /* request cancelled or server shut down */
+
+/* ------------------------------------------------------------------- flags */
+#define BH_DEVICE_PTRS  0x1u  /* pointer arguments are device pointers */
+#define BH_POTENTIAL    0x2u  /* the walk also accumulates phi (needed for PE) */
+#define BH_NO_KAHAN     0x4u  /* plain FP32 force sums instead of Kahan sums */
+
+#define BH_MAX_DEPTH 21       /* levels below the root; fixed by the key width */
+
+/* Solver parameters of one system.
+ *   G      gravitational constant (> 0)
+ *   eps    Plummer softening length (>= 0; 0 allowed, coincident pairs are
+ *          then skipped)
+ *   theta  opening parameter (>= 0; 0 = direct summation through the tree)
+ *   max_depth must be BH_MAX_DEPTH, leaf_cap must be 1 (one particle per
+ *          leaf, Section I; only coincident points share a leaf)
+ *   flags  BH_POTENTIAL, BH_NO_KAHAN */
+typedef struct bh_params {
+    double G, eps, theta;
+    int max_depth;
+    int leaf_cap;
+    unsigned flags;
+} bh_params;
+
+/* One node of the exported canonical tree: depth-first pre-order, children
+ * in octant order 4x+2y+z, which is Morton order of (level, prefix).
+ *   prefix    the node's top 3*level key bits
+ *   first     index of its first particle in sorted (key, input index) order
+ *   count     particles in the node
+ *   level     0 = root ... 21
+ *   childmask bit o set when the child in octant o exists (0 for leaves) */
+typedef struct bh_node {
+    uint64_t prefix;
+    uint32_t first;
+    uint32_t count;
+    uint8_t level;
+    uint8_t childmask;
+    uint8_t pad[6];
+} bh_node;
+
+/* Walk launch shape (the autotuner's search space).
+ *   ppl             particles per lane (1, 2 or 4): a warp task is a tile of
+ *                   32*ppl consecutive Morton-sorted particles
+ *   warps_per_block 2..16
+ *   blocks_per_sm   0 = as many as fit */
+typedef struct bh_tuning {
+    int ppl;
+    int warps_per_block;
+    int blocks_per_sm;
+    int reserved;
+} bh_tuning;
+
+typedef struct bh_system bh_system;
+typedef struct bh_forest bh_forest;
+typedef struct bh_server bh_server;
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *bh_last_error(void);
+
+/* Library version string. */
+const char *bh_version(void);
+
+/* Fills *p with G = 1, eps = 0.01, theta = 0.5, max_depth = 21, leaf_cap = 1,
+ * flags = 0. */
+int bh_params_default(bh_params *p);
+
+/* ---------------------------------------------------------- single system */
+
+/* Creates a system of n >= 1 particles and copies its state to the device.
+ * pos_mass: n x 4 (x, y, z, m), masses > 0 and coordinates finite (checked;
+ * BH_ERR_INVALID otherwise).  vel: n x 4 or NULL (zero velocities).
+ * stream: a cudaStream_t to run on, or NULL for a stream the library creates.
+ * flags: BH_DEVICE_PTRS when pos_mass / vel are device pointers.
+ * The library owns the device state until bh_destroy. */
+int bh_create(bh_system **out, const bh_params *p, int64_t n, const float *pos_mass,
+              const float *vel, void *stream, unsigned flags);
+
+int bh_destroy(bh_system *s);
+
+/* Replaces positions/masses and velocities (n x 4 each; vel may be NULL to
+ * keep the current velocities).  Invalidates the stored accelerations. */
+int bh_set_state(bh_system *s, const float *pos_mass, const float *vel, unsigned flags);
+
+/* Builds the octree of the current positions (Section I; the tree-build
+ * barrier of Section III): bounding cube and root centre of mass (FP64),
+ * Morton keys, radix sort by (key, input index), canonical topology with the
+ * depth cap, bottom-up masses and centres of mass (FP32). */
+int bh_build_tree(bh_system *s);
+
+/* Copies the last built tree to host memory (for parity checks).
+ * keys: n sorted keys or NULL; order: n input indices in sorted order or NULL;
+ * nodes: node_cap entries or NULL; com_m: node_cap x 4 floats (centre of
+ * mass, mass) or NULL.  *n_nodes receives the node count; BH_ERR_INVALID if it
+ * exceeds node_cap while nodes or com_m is given.  cube (4 floats: lo_x,
+ * lo_y, lo_z, side) may be NULL. */
+int bh_get_tree(bh_system *s, uint64_t *keys, uint32_t *order, bh_node *nodes,
+                float *com_m, int64_t node_cap, int64_t *n_nodes, float *cube);
+
+/* Builds the tree and walks it (Section III: the force computation):
+ * a_i = G sum over accepted cells and leaf particles of
+ * m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2), per particle exactly as the
+ * opening test decides for that particle.  The result is kept as the
+ * system's acceleration; if acc_out is not NULL it also receives n x 4 floats
+ * (ax, ay, az, phi; phi is 0 unless BH_POTENTIAL). */
+int bh_compute_accel(bh_system *s, float *acc_out, unsigned flags);
+
+/* Advances nsteps kick-drift-kick leapfrog steps of size dt, rebuilding the
+ * tree every step.  Computes the initial acceleration first if the system has
+ * none.  use_graph != 0 captures the step loop in a CUDA graph (cached per
+ * nsteps and dt).  A node-buffer overflow inside a step is detected on the
+ * device, the step is rolled back, the buffer grown and the step redone. */
+int bh_step(bh_system *s, int nsteps, double dt, int use_graph);
+
+/* Copies the state out (each pointer may be NULL). */
+int bh_get_state(bh_system *s, float *pos_mass, float *vel, float *acc, unsigned flags);
+
+/* FP64 conserved quantities out[8] = {KE, PE, Px, Py, Pz, COMx, COMy, COMz}.
+ * PE needs phi from the last walk (BH_POTENTIAL); it is NaN otherwise. */
+int bh_diagnostics(bh_system *s, double out[8]);
+
+/* Walks the current tree once more counting, per particle, the accepted
+ * cells plus leaf particles it interacts with (its own leaf included).
+ * counts: n uint32 in input order or NULL; *total receives the sum. */
+int bh_interaction_count(bh_system *s, uint32_t *counts, uint64_t *total);
+
+/* Walk launch shape: set explicitly, or pick by timing the candidates on the
+ * current tree (cached per device, log2 N bucket and theta bucket).  Results
+ * do not depend on the shape. */
+int bh_set_tuning(bh_system *s, const bh_tuning *t);
+int bh_get_tuning(bh_system *s, bh_tuning *t);
+int bh_autotune(bh_system *s, bh_tuning *best);
+
+/* ------------------------------------------------------------- profiling */
+
+#define BH_NPHASE 3  /* 0 integrate (kicks, drift), 1 tree build, 2 walk */
+
+/* Starts recording CUDA events around the phases of each step on the
+ * system's stream. */
+int bh_profile_begin(bh_system *s);
+/* Stops recording; phase_ms[BH_NPHASE] receives the summed device time of
+ * each phase, *steps the steps recorded, *launches the kernels launched. */
+int bh_profile_end(bh_system *s, double *phase_ms, int64_t *steps, int64_t *launches);
+
+/* ------------------------------------------------------------------ forest */
+
+/* One system of a forest.  dt is the step size used when bh_forest_step is
+ * given dt <= 0. */
+typedef struct bh_system_desc {
+    int64_t n;
+    const float *pos_mass;  /* n x 4 */
+    const float *vel;       /* n x 4 or NULL */
+    double G, eps, theta, dt;
+} bh_system_desc;
+
+/* Many independent systems sharing one set of launches per step: a segmented
+ * sort, one topology / centre-of-mass pass and one persistent walk launch
+ * over all trees.  Each system's tree and accelerations are the same as it
+ * would get alone.  flags: BH_DEVICE_PTRS, BH_POTENTIAL, BH_NO_KAHAN. */
+int bh_forest_create(bh_forest **out, int nsys, const bh_system_desc *d, void *stream,
+                     unsigned flags);
+int bh_forest_destroy(bh_forest *f);
+int bh_forest_compute_accel(bh_forest *f);
+/* nsteps KDK steps for every system (dt > 0 overrides each system's dt);
+ * use_graph != 0 captures the nsteps loop in one CUDA graph. */
+int bh_forest_step(bh_forest *f, int nsteps, double dt, int use_graph);
+int bh_forest_get_state(bh_forest *f, int sys, float *pos_mass, float *vel, float *acc,
+                        unsigned flags);
+int bh_forest_set_tuning(bh_forest *f, const bh_tuning *t);
+int bh_forest_autotune(bh_forest *f, bh_tuning *best);
+/* Total particles and node count of the last build. */
+int bh_forest_info(bh_forest *f, int64_t *n_total, int64_t *n_nodes);
+
+/* ------------------------------------------------------------------ server */
+
+/* A solve request: particles (host arrays, copied at submit), parameters,
+ * step count (0 = one force evaluation only) and step size. */
+typedef struct bh_request {
+    int64_t n;
+    const float *pos_mass;  /* n x 4, host */
+    const float *vel;       /* n x 4 or NULL, host */
+    double G, eps, theta, dt;
+    int nsteps;
+    unsigned flags;         /* BH_POTENTIAL, BH_NO_KAHAN */
+} bh_request;
+
+/* Result of a finished request.  Output arrays are supplied by the caller
+ * (host, n x 4 each, may be NULL) and filled by bh_poll. */
+typedef struct bh_result {
+    int status;             /* BH_OK or the request's error */
+    int pad;
+    float *pos_mass;
+    float *vel;
+    float *acc;
+    double submit_s;        /* times on the server's monotonic clock */
+    double admit_s;
+    double done_s;
+    int64_t steps_done;
+} bh_result;
+
+typedef struct bh_server_stats {
+    int64_t submitted, admitted, completed, rejected;
+    int64_t ticks;                /* forest steps run */
+    int64_t particle_steps;       /* sum over ticks of resident particles stepped */
+    int64_t resident_systems;
+    int64_t peak_resident_systems;
+    int64_t resident_bytes, peak_resident_bytes;
+    double busy_s;                /* time spent running ticks */
+} bh_server_stats;
+
+/* Starts a server thread that admits requests while their device memory
+ * fits hbm_budget bytes and a slot is free (max_slots), keeps admitted
+ * systems resident on the device, and runs one forest step per tick over
+ * every resident system: a request arriving while others run joins the
+ * batch at the next tick (continuous batching).  stream may be NULL. */
+int bh_server_create(bh_server **out, size_t hbm_budget, int max_slots, void *stream,
+                     unsigned flags);
+/* Queues a request; *ticket identifies it.  BH_ERR_BUDGET if the request
+ * alone exceeds the budget. */
+int bh_submit(bh_server *s, const bh_request *r, uint64_t *ticket);
+/* BH_PENDING while the request runs; BH_OK once done, with res filled and
+ * the ticket released.  Returns the request's own error if it failed. */
+int bh_poll(bh_server *s, uint64_t ticket, bh_result *res);
+/* Waits up to timeout_s seconds for the ticket (BH_ERR_TIMEOUT if it does
+ * not finish), then behaves like bh_poll. */
+int bh_wait(bh_server *s, uint64_t ticket, bh_result *res, double timeout_s);
+int bh_server_stats_get(bh_server *s, bh_server_stats *st);
+/* Seconds on the server's monotonic clock (the clock of bh_result times). */
+double bh_server_now(bh_server *s);
+/* Stops the thread; pending and running requests end with BH_ERR_CANCELLED. */
+int bh_server_destroy(bh_server *s);
+
+/* ---------------------------------------------------------- micro-benchmarks */
+
+/* Measured FP32 non-tensor throughput: a kernel of independent FMA chains on
+ * every SM; *gflops = 2 x FMAs / time. */
+int bh_micro_fma_peak(double *gflops, void *stream);
+/* Measured device copy bandwidth over a buffer of `bytes` (read + write
+ * counted). */
+int bh_micro_copy_bw(size_t bytes, double *gbs, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BH_H */

@@ -1,0 +1,178 @@
+// bh_internal.cuh -- device data layout and kernel launchers shared by the
+// library's translation units.  Not part of the public ABI (see include/bh.h).
+//
+// Layout in HBM (one "forest" = one or more independent systems):
+//   * Per system, in the caller's particle order: pos (x,y,z,m), vel, acc
+//     (ax,ay,az,phi) as float4 arrays, plus a backup of pos/vel taken at the
+//     start of every step (used to roll a step back after a node-buffer
+//     overflow).
+//   * Systems are concatenated in a "virtual" index space [0, n_total);
+//     system s owns [start_s, start_s + n_s).  Every O(n) kernel runs over
+//     chunks of <= kChunk particles that never straddle two systems, so a
+//     block finds its system with one table lookup.
+//   * Sorted working arrays in virtual index space: 64-bit keys and 32-bit
+//     virtual ids (double-buffered for the radix sort), the Morton-ordered
+//     copy spos of pos_mass, per-particle node counts / offsets.
+//   * Nodes of all trees in one array, each system's nodes contiguous, in
+//     depth-first pre-order (the canonical order): nodeA = (com_x, com_y,
+//     com_z, mass) and nodeB = (skip, crit2 bits, first, count), where skip
+//     is the index of the next node after the subtree and crit2 = s^2/theta^2
+//     (accept iff d^2 > crit2), -1 for a one-particle leaf (always taken as
+//     is) and -2 for a depth-cap bucket (particles one by one).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bh {
+
+constexpr int kLevels = BH_MAX_DEPTH;  // 21
+constexpr int kNumLevels = kLevels + 1;
+constexpr int kChunk = 4096;
+constexpr int kChunkThreads = 256;
+constexpr int kItems = kChunk / kChunkThreads;  // 16
+constexpr float kLeafCrit = -1.0f;
+constexpr float kBucketCrit = -2.0f;
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kRadixPasses = 8;  // 63-bit keys
+constexpr int kScanTile = 2048;
+
+// device status codes (0 = ok)
+enum : int { ST_OK = 0, ST_CAPACITY = 1, ST_WALK_LIMIT = 2, ST_BAD_INPUT = 3 };
+
+// per-system modes of one step
+enum : int { MODE_ACCEL = 0, MODE_KDK = 1, MODE_IDLE = 2 };
+
+struct SysStatic {
+    float4 *pos, *vel, *acc, *bpos, *bvel;
+    int start, n;
+    int chunk0, nchunk;
+    float eps2, G, inv_theta2, half_dt;
+    float dt;
+    int flags;
+    int pad[2];
+};
+
+struct SysDyn {
+    float lo[3];
+    float side;
+    float scale;
+    float root_m;
+    float root_com[3];
+    float pad;
+    double mtot;
+    double mx[3];
+};
+
+struct ChunkPart {
+    float mn[3];
+    float mx[3];
+    float pad[2];
+    double m, sx, sy, sz;
+};
+
+struct DiagPart {
+    double v[9];  // KE, PE, Px, Py, Pz, M, Mx, My, Mz
+    double pad;
+};
+
+// Small per-forest device scalars.  The block [queue .. level_cur] is zeroed
+// at the start of every step with one memset.
+struct Small {
+    int status;
+    unsigned M;
+    unsigned needed;
+    unsigned steps_done;
+    unsigned long long icount;
+    unsigned queue;
+    unsigned level_cnt[kNumLevels];
+    unsigned level_cur[kNumLevels];
+    unsigned level_off[kNumLevels + 1];
+};
+
+struct Tile {
+    int start;  // virtual index of the first particle (sorted order)
+    int count;  // <= 32 * ppl
+    int sys;
+    int pad;
+};
+
+// ------------------------------------------------------------- launchers
+
+struct BuildBufs {
+    const int4 *chunks;  // (sys, start, count, 0)
+    int nchunks;
+    const SysStatic *sys;
+    SysDyn *dyn;
+    int nsys;
+    const int *mode;  // per system
+    ChunkPart *parts;
+    uint64_t *key0, *key1;
+    uint32_t *val0, *val1;
+    uint32_t *rs_counts;  // kRadixBins * nchunks
+    uint32_t *scan_part;  // scan partials
+    float4 *spos;
+    uint32_t *ncount;     // n_total + 1
+    uint32_t *noff;       // n_total + 1
+    float4 *nodeA;
+    int4 *nodeB;
+    uint8_t *nlevel;
+    uint32_t *nlist;
+    unsigned node_cap;
+    Small *small;
+    int n_total;
+    int nsm;
+};
+
+void launch_kick_drift_bbox(const BuildBufs &b, cudaStream_t st);
+void launch_bbox_final(const BuildBufs &b, cudaStream_t st);
+void launch_keys(const BuildBufs &b, cudaStream_t st);
+void launch_sort(const BuildBufs &b, cudaStream_t st);
+void launch_permute(const BuildBufs &b, cudaStream_t st);
+void launch_topology(const BuildBufs &b, cudaStream_t st);
+void launch_com(const BuildBufs &b, cudaStream_t st);
+void launch_kick(const BuildBufs &b, cudaStream_t st);
+void launch_restore(const BuildBufs &b, cudaStream_t st);
+void launch_validate(const BuildBufs &b, cudaStream_t st);
+void launch_diagnostics(const BuildBufs &b, DiagPart *parts, double *out, cudaStream_t st);
+void launch_export(const BuildBufs &b, int sys, bh_node *nodes_dev, float4 *com_dev,
+                   uint32_t *order_dev, cudaStream_t st);
+
+// generic exclusive scan of n uint32 (out may alias in); total -> *total
+void launch_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *partials,
+                 uint32_t *total, const int *status, cudaStream_t st);
+
+struct WalkArgs {
+    const float4 *nodeA;
+    const int4 *nodeB;
+    const float4 *spos;
+    const uint32_t *sid;  // sorted -> virtual id
+    const uint32_t *noff;
+    const Tile *tiles;
+    int ntiles;
+    const SysStatic *sys;
+    const int *mode;
+    Small *small;
+    uint32_t *counts;  // per-particle interaction counts (virtual order) or null
+};
+
+struct WalkShape {
+    int ppl;
+    int warps;
+    int blocks_per_sm;
+};
+
+// kahan / potential / counting variants; returns number of kernel launches
+int launch_walk(const WalkArgs &a, const WalkShape &sh, bool kahan, bool pot, bool count,
+                int nsm, cudaStream_t st);
+int walk_max_blocks_per_sm(const WalkShape &sh, bool kahan, bool pot);
+
+// micro-benchmarks
+double micro_fma_gflops(cudaStream_t st);
+double micro_copy_gbs(size_t bytes, cudaStream_t st);
+
+// number of kernel launches issued by the last launch_* helper call on
+// this thread (used for the launch count reported by profiling)
+extern thread_local int g_launches;
+
+}  // namespace bh

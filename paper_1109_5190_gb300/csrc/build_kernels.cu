@@ -1,0 +1,726 @@
+// build_kernels.cu -- per-step O(n) kernels of the Barnes-Hut hot path:
+// leapfrog kick/drift fused with the bounding-box / root reductions, Morton
+// keys, the gather into Morton order, the octree topology, the bottom-up
+// centre-of-mass pass, the closing kick, diagnostics and the tree export.
+//
+// Paper: Dekate et al., arXiv:1109.5190.  Section I: particles grouped by a
+// hierarchy of cubes subdivided until there is one particle per sub-cube,
+// with a centre of mass per cube; Section III: the tree is rebuilt from all
+// positions in every iteration (a global barrier), then forces are computed.
+// Every kernel here is HBM-bound streaming work (no tensor cores): loads are
+// coalesced float4, one block per chunk of <= 4096 particles of one system.
+#include "bh.h"
+#include "bh_internal.cuh"
+
+namespace bh {
+
+thread_local int g_launches = 0;
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ bool halted(const Small *sm) { return sm->status != ST_OK; }
+
+// Deterministic block reduction helpers (fixed shuffle tree, then warps in
+// order by thread 0): results depend only on blockDim and the inputs.
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_min(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_down_sync(FULL, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(FULL, v, o));
+    return v;
+}
+
+struct BoxAcc {
+    float mn[3], mx[3];
+    double m, s[3];
+};
+
+__device__ __forceinline__ void box_init(BoxAcc &b)
+{
+    for (int a = 0; a < 3; ++a) {
+        b.mn[a] = __int_as_float(0x7f800000);   // +inf
+        b.mx[a] = __int_as_float(0xff800000);   // -inf
+        b.s[a] = 0.0;
+    }
+    b.m = 0.0;
+}
+
+// Reduces BoxAcc over the block; the result is valid in thread 0.
+__device__ BoxAcc box_block_reduce(BoxAcc b)
+{
+    __shared__ float smn[3][32], smx[3][32];
+    __shared__ double sm[4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int a = 0; a < 3; ++a) {
+        b.mn[a] = warp_min(b.mn[a]);
+        b.mx[a] = warp_max(b.mx[a]);
+        b.s[a] = warp_sum(b.s[a]);
+    }
+    b.m = warp_sum(b.m);
+    if (lane == 0) {
+        for (int a = 0; a < 3; ++a) {
+            smn[a][w] = b.mn[a];
+            smx[a][w] = b.mx[a];
+            sm[a][w] = b.s[a];
+        }
+        sm[3][w] = b.m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < nw; ++k) {
+            for (int a = 0; a < 3; ++a) {
+                b.mn[a] = fminf(b.mn[a], smn[a][k]);
+                b.mx[a] = fmaxf(b.mx[a], smx[a][k]);
+                b.s[a] += sm[a][k];
+            }
+            b.m += sm[3][k];
+        }
+    }
+    return b;
+}
+
+// ------------------------------------------------ kick + drift + box (A8/A1)
+
+// Leapfrog opening half: v += a dt/2, x += v dt (after saving x, v for a
+// possible roll-back), fused with the per-chunk partial reductions of the new
+// positions: FP32 min/max (exact) and FP64 mass and mass-weighted position
+// sums (root centre of mass).
+__global__ void __launch_bounds__(kChunkThreads)
+k_kick_drift_box(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+                 const int *__restrict__ mode, ChunkPart *__restrict__ parts,
+                 const Small *__restrict__ sm)
+{
+    if (halted(sm)) return;
+    const int4 c = chunks[blockIdx.x];
+    const SysStatic S = sys[c.x];
+    const bool kdk = mode[c.x] == MODE_KDK;
+    const int loc0 = c.y - S.start;
+    BoxAcc b;
+    box_init(b);
+    for (int k = 0; k < kItems; ++k) {
+        const int i = k * kChunkThreads + threadIdx.x;
+        if (i >= c.z) break;
+        const int li = loc0 + i;
+        float4 p = S.pos[li];
+        if (kdk) {
+            float4 v = S.vel[li];
+            const float4 a = S.acc[li];
+            S.bpos[li] = p;
+            S.bvel[li] = v;
+            v.x = fmaf(a.x, S.half_dt, v.x);
+            v.y = fmaf(a.y, S.half_dt, v.y);
+            v.z = fmaf(a.z, S.half_dt, v.z);
+            p.x = fmaf(v.x, S.dt, p.x);
+            p.y = fmaf(v.y, S.dt, p.y);
+            p.z = fmaf(v.z, S.dt, p.z);
+            S.vel[li] = v;
+            S.pos[li] = p;
+        }
+        b.mn[0] = fminf(b.mn[0], p.x); b.mx[0] = fmaxf(b.mx[0], p.x);
+        b.mn[1] = fminf(b.mn[1], p.y); b.mx[1] = fmaxf(b.mx[1], p.y);
+        b.mn[2] = fminf(b.mn[2], p.z); b.mx[2] = fmaxf(b.mx[2], p.z);
+        const double m = (double)p.w;
+        b.m += m;
+        b.s[0] = fma(m, (double)p.x, b.s[0]);
+        b.s[1] = fma(m, (double)p.y, b.s[1]);
+        b.s[2] = fma(m, (double)p.z, b.s[2]);
+    }
+    b = box_block_reduce(b);
+    if (threadIdx.x == 0) {
+        ChunkPart out;
+        for (int a = 0; a < 3; ++a) { out.mn[a] = b.mn[a]; out.mx[a] = b.mx[a]; }
+        out.pad[0] = out.pad[1] = 0.f;
+        out.m = b.m; out.sx = b.s[0]; out.sy = b.s[1]; out.sz = b.s[2];
+        parts[blockIdx.x] = out;
+    }
+}
+
+// Per system: combine the chunk partials in a fixed order; derive the key
+// cube (lo = per-axis minimum, side = largest FP32 extent, 1 if < 1e-30,
+// scale = RN32(2^21 / side)) and the FP64 root mass and centre of mass.
+__global__ void __launch_bounds__(256)
+k_box_final(const SysStatic *__restrict__ sys, SysDyn *__restrict__ dyn,
+            const ChunkPart *__restrict__ parts, const Small *__restrict__ sm)
+{
+    if (halted(sm)) return;
+    const SysStatic S = sys[blockIdx.x];
+    BoxAcc b;
+    box_init(b);
+    for (int k = threadIdx.x; k < S.nchunk; k += blockDim.x) {
+        const ChunkPart p = parts[S.chunk0 + k];
+        for (int a = 0; a < 3; ++a) {
+            b.mn[a] = fminf(b.mn[a], p.mn[a]);
+            b.mx[a] = fmaxf(b.mx[a], p.mx[a]);
+        }
+        b.m += p.m; b.s[0] += p.sx; b.s[1] += p.sy; b.s[2] += p.sz;
+    }
+    b = box_block_reduce(b);
+    if (threadIdx.x == 0) {
+        SysDyn d;
+        float side = 0.0f;
+        for (int a = 0; a < 3; ++a) {
+            const float e = __fsub_rn(b.mx[a], b.mn[a]);
+            if (e > side) side = e;
+            d.lo[a] = b.mn[a];
+        }
+        if (!(side >= 1e-30f)) side = 1.0f;
+        d.side = side;
+        d.scale = __fdiv_rn(2097152.0f, side);
+        d.mtot = b.m;
+        for (int a = 0; a < 3; ++a) d.mx[a] = b.s[a];
+        d.root_m = (float)b.m;
+        for (int a = 0; a < 3; ++a) d.root_com[a] = (float)(b.s[a] / b.m);
+        d.pad = 0.f;
+        dyn[blockIdx.x] = d;
+    }
+}
+
+// ----------------------------------------------------------- keys (A2)
+
+__device__ __forceinline__ uint32_t quantise(float x, float lo, float scale)
+{
+    const float d = __fsub_rn(x, lo);
+    const float t = __fmul_rn(d, scale);
+    const float f = floorf(t);
+    if (!(f > 0.0f)) return 0u;
+    if (f >= 2097151.0f) return 2097151u;
+    return (uint32_t)f;
+}
+
+// Spreads the 21 low bits of v so bit b lands at bit 3b.
+__device__ __forceinline__ uint64_t spread3(uint32_t v)
+{
+    uint64_t x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+// Key of every particle in input order, value = its virtual id, so the stable
+// radix sort orders equal keys by input index.
+__global__ void __launch_bounds__(kChunkThreads)
+k_keys(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+       const SysDyn *__restrict__ dyn, uint64_t *__restrict__ key, uint32_t *__restrict__ val,
+       const Small *__restrict__ sm)
+{
+    if (halted(sm)) return;
+    const int4 c = chunks[blockIdx.x];
+    const SysStatic S = sys[c.x];
+    const SysDyn D = dyn[c.x];
+    const int loc0 = c.y - S.start;
+    for (int k = 0; k < kItems; ++k) {
+        const int i = k * kChunkThreads + threadIdx.x;
+        if (i >= c.z) break;
+        const float4 p = S.pos[loc0 + i];
+        const uint32_t qx = quantise(p.x, D.lo[0], D.scale);
+        const uint32_t qy = quantise(p.y, D.lo[1], D.scale);
+        const uint32_t qz = quantise(p.z, D.lo[2], D.scale);
+        key[c.y + i] = (spread3(qx) << 2) | (spread3(qy) << 1) | spread3(qz);
+        val[c.y + i] = (uint32_t)(c.y + i);
+    }
+}
+
+// ----------------------------------------------------------- permute (A4)
+
+__global__ void __launch_bounds__(kChunkThreads)
+k_permute(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+          const uint32_t *__restrict__ sid, float4 *__restrict__ spos,
+          const Small *__restrict__ sm)
+{
+    if (halted(sm)) return;
+    const int4 c = chunks[blockIdx.x];
+    const SysStatic S = sys[c.x];
+    for (int k = 0; k < kItems; ++k) {
+        const int i = k * kChunkThreads + threadIdx.x;
+        if (i >= c.z) break;
+        const int j = c.y + i;
+        spos[j] = __ldg(&S.pos[(int)sid[j] - S.start]);
+    }
+}
+
+// ---------------------------------------------------------- topology (A5)
+
+// Number of leading octal digits (levels) two keys share: 0..21.
+__device__ __forceinline__ int common_levels(uint64_t a, uint64_t b)
+{
+    const uint64_t x = a ^ b;
+    if (!x) return kLevels;
+    const int p = 63 - __clzll((long long)x);
+    return (kLevels - 1) - p / 3;
+}
+
+// For sorted particle j of a system [a, b): dprev / dnext = levels shared
+// with its neighbours (-1 at the system's ends).  The cells that start at j
+// are the levels dprev+1 .. 21; such a cell is a node iff its parent holds
+// >= 2 particles, i.e. iff level - 1 <= max(dprev, dnext); the deepest of
+// them is a leaf (one particle, or the level-21 bucket of equal keys).
+struct Span {
+    int dprev, dnext, lmax, cnt;
+};
+
+__device__ __forceinline__ Span node_span(const uint64_t *__restrict__ key, int j, int a, int b)
+{
+    Span s;
+    const uint64_t kj = key[j];
+    s.dprev = (j == a) ? -1 : common_levels(key[j - 1], kj);
+    s.dnext = (j == b - 1) ? -1 : common_levels(kj, key[j + 1]);
+    if (s.dprev >= kLevels) {
+        s.lmax = s.dprev;
+        s.cnt = 0;
+    } else {
+        s.lmax = min(kLevels, max(s.dprev, s.dnext) + 1);
+        s.cnt = s.lmax - s.dprev;
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(kChunkThreads)
+k_topo_count(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+             const uint64_t *__restrict__ key, uint32_t *__restrict__ ncount,
+             Small *__restrict__ sm)
+{
+    if (halted(sm)) return;
+    __shared__ unsigned h[kNumLevels];
+    if (threadIdx.x < kNumLevels) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int4 c = chunks[blockIdx.x];
+    const SysStatic S = sys[c.x];
+    for (int k = 0; k < kItems; ++k) {
+        const int i = k * kChunkThreads + threadIdx.x;
+        if (i >= c.z) break;
+        const int j = c.y + i;
+        const Span s = node_span(key, j, S.start, S.start + S.n);
+        ncount[j] = (uint32_t)s.cnt;
+        for (int l = s.dprev + 1; l <= s.lmax; ++l) atomicAdd(&h[l], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumLevels && h[threadIdx.x])
+        atomicAdd(&sm->level_cnt[threadIdx.x], h[threadIdx.x]);
+}
+
+// Node count check and per-level list offsets (one thread).
+__global__ void k_level_offsets(Small *__restrict__ sm, const uint32_t *__restrict__ noff,
+                                int n_total, unsigned cap)
+{
+    if (halted(sm) || threadIdx.x != 0) return;
+    const unsigned M = noff[n_total];
+    sm->M = M;
+    if (M > cap) {
+        sm->needed = M;
+        sm->status = ST_CAPACITY;
+        return;
+    }
+    unsigned off = 0;
+    for (int l = 0; l < kNumLevels; ++l) {
+        sm->level_off[l] = off;
+        off += sm->level_cnt[l];
+    }
+    sm->level_off[kNumLevels] = off;
+}
+
+// First index e in [lo, b] whose key leaves the level-l cell of kj (all
+// indices below lo are known to be inside): galloping then bisection.
+__device__ __forceinline__ int cell_end(const uint64_t *__restrict__ key, uint64_t kj, int lo,
+                                        int b, int l)
+{
+    const int sh = 3 * (kLevels - l);
+    int step = 1, hi;
+    for (;;) {
+        const int p = lo + step - 1;
+        if (p >= b) { hi = b; break; }
+        if (((key[p] ^ kj) >> sh) != 0) { hi = p; break; }
+        lo = p + 1;
+        step <<= 1;
+    }
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (((key[mid] ^ kj) >> sh) != 0) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ float pow2_neg(int l) { return __int_as_float((127 - l) << 23); }
+
+// Writes every node that starts at a particle: skip pointer (the first node
+// starting at the cell's end particle), opening threshold, first, count and
+// level, plus its slot in its level's list.  Root centres of mass come from
+// the FP64 reduction (or the particle itself for a one-particle system).
+__global__ void __launch_bounds__(kChunkThreads)
+k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+             const SysDyn *__restrict__ dyn, const uint64_t *__restrict__ key,
+             const uint32_t *__restrict__ noff, const float4 *__restrict__ spos,
+             float4 *__restrict__ nodeA, int4 *__restrict__ nodeB,
+             uint8_t *__restrict__ nlevel, uint32_t *__restrict__ nlist, Small *__restrict__ sm)
+{
+    if (halted(sm)) return;
+    __shared__ unsigned h[kNumLevels], base[kNumLevels];
+    if (threadIdx.x < kNumLevels) h[threadIdx.x] = 0;
+    __syncthreads();
+    const int4 c = chunks[blockIdx.x];
+    const SysStatic S = sys[c.x];
+    const int a = S.start, b = S.start + S.n;
+    for (int k = 0; k < kItems; ++k) {
+        const int i = k * kChunkThreads + threadIdx.x;
+        if (i >= c.z) break;
+        const Span s = node_span(key, c.y + i, a, b);
+        for (int l = s.dprev + 1; l <= s.lmax; ++l) atomicAdd(&h[l], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumLevels) {
+        const unsigned cnt = h[threadIdx.x];
+        base[threadIdx.x] = (cnt ? atomicAdd(&sm->level_cur[threadIdx.x], cnt) : 0u) +
+                            sm->level_off[threadIdx.x];
+        h[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    const SysDyn D = dyn[c.x];
+    for (int k = 0; k < kItems; ++k) {
+        const int i = k * kChunkThreads + threadIdx.x;
+        if (i >= c.z) break;
+        const int j = c.y + i;
+        const Span s = node_span(key, j, a, b);
+        if (s.cnt == 0) continue;
+        const uint64_t kj = key[j];
+        const unsigned nb = noff[j];
+        int end = j + 1;
+        for (int l = s.lmax; l > s.dprev; --l) {
+            const unsigned n = nb + (unsigned)(l - s.dprev - 1);
+            if (l <= s.dnext) end = cell_end(key, kj, max(end, j + 2), b, l);
+            else end = j + 1;
+            const int count = end - j;
+            float crit;
+            if (count == 1) {
+                crit = kLeafCrit;
+            } else if (l == kLevels) {
+                crit = kBucketCrit;
+            } else {
+                const float sl = __fmul_rn(D.side, pow2_neg(l));
+                crit = __fmul_rn(__fmul_rn(sl, sl), S.inv_theta2);
+            }
+            nodeB[n] = make_int4((int)noff[end], __float_as_int(crit), j, count);
+            nlevel[n] = (uint8_t)l;
+            nlist[base[l] + atomicAdd(&h[l], 1u)] = n;
+            if (l == 0) {
+                nodeA[n] = (count == 1) ? spos[j]
+                                        : make_float4(D.root_com[0], D.root_com[1],
+                                                      D.root_com[2], D.root_m);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------- centre of mass (A6)
+
+// Bottom-up, one launch per level (deepest first): a one-particle leaf takes
+// its particle; a bucket sums its particles; an internal node sums its
+// children (first child = next node, then skip pointers), each relative to
+// the first child's centre to keep FP32 cancellation small.
+__global__ void __launch_bounds__(256)
+k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
+            float4 *__restrict__ nodeA, const int4 *__restrict__ nodeB,
+            const Small *__restrict__ sm)
+{
+    if (halted(sm)) return;
+    const unsigned cnt = sm->level_cnt[l];
+    const unsigned off = sm->level_off[l];
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
+        const unsigned n = nlist[off + k];
+        const int4 B = nodeB[n];
+        const float crit = __int_as_float(B.y);
+        if (crit == kLeafCrit) {
+            nodeA[n] = spos[B.z];
+            continue;
+        }
+        float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+        float ox, oy, oz;
+        if (crit == kBucketCrit) {
+            const float4 o = spos[B.z];
+            ox = o.x; oy = o.y; oz = o.z;
+            for (int q = B.z; q < B.z + B.w; ++q) {
+                const float4 p = spos[q];
+                M += p.w;
+                sx = fmaf(p.w, p.x - ox, sx);
+                sy = fmaf(p.w, p.y - oy, sy);
+                sz = fmaf(p.w, p.z - oz, sz);
+            }
+        } else {
+            int ch = (int)n + 1;
+            const float4 o = nodeA[ch];
+            ox = o.x; oy = o.y; oz = o.z;
+            while (ch < B.x) {
+                const float4 p = nodeA[ch];
+                M += p.w;
+                sx = fmaf(p.w, p.x - ox, sx);
+                sy = fmaf(p.w, p.y - oy, sy);
+                sz = fmaf(p.w, p.z - oz, sz);
+                ch = nodeB[ch].x;
+            }
+        }
+        nodeA[n] = make_float4(ox + sx / M, oy + sy / M, oz + sz / M, M);
+    }
+}
+
+// ------------------------------------------------------ closing kick (A8)
+
+__global__ void __launch_bounds__(kChunkThreads)
+k_kick(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+       const int *__restrict__ mode, Small *__restrict__ sm)
+{
+    if (halted(sm)) return;
+    const int4 c = chunks[blockIdx.x];
+    if (blockIdx.x == 0 && threadIdx.x == 0) sm->steps_done += 1;
+    if (mode[c.x] != MODE_KDK) return;
+    const SysStatic S = sys[c.x];
+    const int loc0 = c.y - S.start;
+    for (int k = 0; k < kItems; ++k) {
+        const int i = k * kChunkThreads + threadIdx.x;
+        if (i >= c.z) break;
+        const int li = loc0 + i;
+        float4 v = S.vel[li];
+        const float4 a = S.acc[li];
+        v.x = fmaf(a.x, S.half_dt, v.x);
+        v.y = fmaf(a.y, S.half_dt, v.y);
+        v.z = fmaf(a.z, S.half_dt, v.z);
+        S.vel[li] = v;
+    }
+}
+
+// Rolls back the opening kick/drift of a step that overflowed the node buffer.
+__global__ void __launch_bounds__(kChunkThreads)
+k_restore(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+          const int *__restrict__ mode)
+{
+    const int4 c = chunks[blockIdx.x];
+    if (mode[c.x] != MODE_KDK) return;
+    const SysStatic S = sys[c.x];
+    const int loc0 = c.y - S.start;
+    for (int k = 0; k < kItems; ++k) {
+        const int i = k * kChunkThreads + threadIdx.x;
+        if (i >= c.z) break;
+        S.pos[loc0 + i] = S.bpos[loc0 + i];
+        S.vel[loc0 + i] = S.bvel[loc0 + i];
+    }
+}
+
+// Input check for device-resident inputs: finite coordinates, mass > 0.
+__global__ void __launch_bounds__(kChunkThreads)
+k_validate(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+           Small *__restrict__ sm)
+{
+    const int4 c = chunks[blockIdx.x];
+    const SysStatic S = sys[c.x];
+    const int loc0 = c.y - S.start;
+    bool bad = false;
+    for (int k = 0; k < kItems; ++k) {
+        const int i = k * kChunkThreads + threadIdx.x;
+        if (i >= c.z) break;
+        const float4 p = S.pos[loc0 + i];
+        const float4 v = S.vel[loc0 + i];
+        bad |= !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && p.w > 0.f && isfinite(p.w));
+        bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z));
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&sm->status, ST_BAD_INPUT);
+}
+
+// ------------------------------------------------------ diagnostics (A9)
+
+__global__ void __launch_bounds__(kChunkThreads)
+k_diag_part(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+            DiagPart *__restrict__ parts)
+{
+    const int4 c = chunks[blockIdx.x];
+    const SysStatic S = sys[c.x];
+    const int loc0 = c.y - S.start;
+    double v[9];
+    for (int q = 0; q < 9; ++q) v[q] = 0.0;
+    for (int k = 0; k < kItems; ++k) {
+        const int i = k * kChunkThreads + threadIdx.x;
+        if (i >= c.z) break;
+        const float4 p = S.pos[loc0 + i];
+        const float4 u = S.vel[loc0 + i];
+        const float4 a = S.acc[loc0 + i];
+        const double m = p.w;
+        const double ux = u.x, uy = u.y, uz = u.z;
+        v[0] += 0.5 * m * (ux * ux + uy * uy + uz * uz);
+        v[1] += 0.5 * m * (double)a.w;
+        v[2] += m * ux; v[3] += m * uy; v[4] += m * uz;
+        v[5] += m;
+        v[6] += m * (double)p.x; v[7] += m * (double)p.y; v[8] += m * (double)p.z;
+    }
+    __shared__ double sh[9][kChunkThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int q = 0; q < 9; ++q) {
+        v[q] = warp_sum(v[q]);
+        if (lane == 0) sh[q][w] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DiagPart out;
+        for (int q = 0; q < 9; ++q) {
+            double t = sh[q][0];
+            for (int k = 1; k < kChunkThreads / 32; ++k) t += sh[q][k];
+            out.v[q] = t;
+        }
+        out.pad = 0.0;
+        parts[blockIdx.x] = out;
+    }
+}
+
+__global__ void k_diag_final(const SysStatic *__restrict__ sys, const DiagPart *__restrict__ parts,
+                             double *__restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    const SysStatic S = sys[blockIdx.x];
+    double v[9];
+    for (int q = 0; q < 9; ++q) v[q] = 0.0;
+    for (int k = 0; k < S.nchunk; ++k)
+        for (int q = 0; q < 9; ++q) v[q] += parts[S.chunk0 + k].v[q];
+    double *o = out + 8 * blockIdx.x;
+    o[0] = v[0];
+    o[1] = v[1];
+    o[2] = v[2]; o[3] = v[3]; o[4] = v[4];
+    o[5] = v[6] / v[5]; o[6] = v[7] / v[5]; o[7] = v[8] / v[5];
+}
+
+// ----------------------------------------------------------- export
+
+__global__ void __launch_bounds__(256)
+k_export(int sysid, const SysStatic *__restrict__ sys, const uint32_t *__restrict__ noff,
+         const uint64_t *__restrict__ key, const uint32_t *__restrict__ sid,
+         const float4 *__restrict__ nodeA, const int4 *__restrict__ nodeB,
+         const uint8_t *__restrict__ nlevel, bh_node *__restrict__ out_nodes,
+         float4 *__restrict__ out_com, uint32_t *__restrict__ out_order)
+{
+    const SysStatic S = sys[sysid];
+    const unsigned n0 = noff[S.start], n1 = noff[S.start + S.n];
+    const unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned n = n0 + blockIdx.x * blockDim.x + threadIdx.x; n < n1; n += stride) {
+        const int4 B = nodeB[n];
+        const int l = nlevel[n];
+        const uint64_t pre = (l == 0) ? 0ull : (key[B.z] >> (3 * (kLevels - l)));
+        unsigned cm = 0;
+        const float crit = __int_as_float(B.y);
+        if (crit != kLeafCrit && crit != kBucketCrit) {
+            int ch = (int)n + 1;
+            while (ch < B.x) {
+                const int f = nodeB[ch].z;
+                cm |= 1u << (unsigned)((key[f] >> (3 * (kLevels - l - 1))) & 7u);
+                ch = nodeB[ch].x;
+            }
+        }
+        if (out_nodes) {
+            bh_node o;
+            o.prefix = pre;
+            o.first = (uint32_t)(B.z - S.start);
+            o.count = (uint32_t)B.w;
+            o.level = (uint8_t)l;
+            o.childmask = (uint8_t)cm;
+            for (int q = 0; q < 6; ++q) o.pad[q] = 0;
+            out_nodes[n - n0] = o;
+        }
+        if (out_com) out_com[n - n0] = nodeA[n];
+    }
+    if (out_order) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += stride)
+            out_order[i] = sid[S.start + i] - (uint32_t)S.start;
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers
+
+void launch_kick_drift_bbox(const BuildBufs &b, cudaStream_t st)
+{
+    k_kick_drift_box<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.mode, b.parts, b.small);
+    k_box_final<<<b.nsys, 256, 0, st>>>(b.sys, b.dyn, b.parts, b.small);
+    g_launches += 2;
+}
+
+void launch_bbox_final(const BuildBufs &b, cudaStream_t st)
+{
+    k_box_final<<<b.nsys, 256, 0, st>>>(b.sys, b.dyn, b.parts, b.small);
+    g_launches += 1;
+}
+
+void launch_keys(const BuildBufs &b, cudaStream_t st)
+{
+    k_keys<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.dyn, b.key0, b.val0, b.small);
+    g_launches += 1;
+}
+
+void launch_permute(const BuildBufs &b, cudaStream_t st)
+{
+    k_permute<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.val0, b.spos, b.small);
+    g_launches += 1;
+}
+
+void launch_topology(const BuildBufs &b, cudaStream_t st)
+{
+    k_topo_count<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.key0, b.ncount, b.small);
+    g_launches += 1;
+    launch_scan(b.ncount, b.noff, b.n_total, b.scan_part, b.noff + b.n_total, &b.small->status, st);
+    k_level_offsets<<<1, 32, 0, st>>>(b.small, b.noff, b.n_total, b.node_cap);
+    k_topo_write<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.dyn, b.key0, b.noff,
+                                                      b.spos, b.nodeA, b.nodeB, b.nlevel,
+                                                      b.nlist, b.small);
+    g_launches += 2;
+}
+
+void launch_com(const BuildBufs &b, cudaStream_t st)
+{
+    const int grid = b.nsm * 8;
+    for (int l = kLevels; l >= 1; --l) {
+        k_com_level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeA, b.nodeB, b.small);
+        g_launches += 1;
+    }
+}
+
+void launch_kick(const BuildBufs &b, cudaStream_t st)
+{
+    k_kick<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.mode, b.small);
+    g_launches += 1;
+}
+
+void launch_restore(const BuildBufs &b, cudaStream_t st)
+{
+    k_restore<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.mode);
+    g_launches += 1;
+}
+
+void launch_validate(const BuildBufs &b, cudaStream_t st)
+{
+    k_validate<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.small);
+    g_launches += 1;
+}
+
+void launch_diagnostics(const BuildBufs &b, DiagPart *parts, double *out, cudaStream_t st)
+{
+    k_diag_part<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, parts);
+    k_diag_final<<<b.nsys, 32, 0, st>>>(b.sys, parts, out);
+    g_launches += 2;
+}
+
+void launch_export(const BuildBufs &b, int sysid, bh_node *nodes_dev, float4 *com_dev,
+                   uint32_t *order_dev, cudaStream_t st)
+{
+    k_export<<<b.nsm * 4, 256, 0, st>>>(sysid, b.sys, b.noff, b.key0, b.val0, b.nodeA, b.nodeB,
+                                        b.nlevel, nodes_dev, com_dev, order_dev);
+    g_launches += 1;
+}
+
+}  // namespace bh

@@ -1,0 +1,1434 @@
+// runtime.cu -- host runtime behind the C ABI of include/bh.h.
+//
+// One internal object, Forest, runs every path: a single system is a forest
+// of one; a bh_forest is many systems sharing every launch of a step; the
+// server re-tables its resident systems into a forest at every tick.  A step
+// enqueues, on the forest's own stream:
+//   kick+drift fused with the box / root reductions -> per-system cube ->
+//   Morton keys -> 8-pass segmented radix sort -> gather into Morton order ->
+//   topology (count, scan, capacity check, write) -> centre of mass, one
+//   launch per level -> persistent walk -> closing kick.
+// Node buffers have a capacity; a step whose tree would not fit sets a device
+// status, every later kernel of the run returns at once, and the host rolls
+// the failed step back (positions and velocities saved at its start), grows
+// the buffers and redoes the remaining steps.  Graph mode captures the step
+// loop once per (step count, buffers, launch shape) and replays it.
+#include "bh.h"
+#include "bh_internal.cuh"
+
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <chrono>
+#include <climits>
+#include <cmath>
+#include <condition_variable>
+#include <cstddef>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+using namespace bh;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CKR(call)                                                                        \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            cudaGetLastError();                                                          \
+            return fail(BH_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                \
+    } while (0)
+
+#define TRY(expr)                 \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ != BH_OK) return rc_; \
+    } while (0)
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int ensure(size_t nb)
+    {
+        if (nb == 0) nb = 256;
+        if (p && nb <= bytes) return BH_OK;
+        release();
+        cudaError_t e = cudaMalloc(&p, nb);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            return fail(BH_ERR_OOM, "cudaMalloc of " + std::to_string(nb) + " bytes failed: " +
+                                        cudaGetErrorString(e));
+        }
+        bytes = nb;
+        return BH_OK;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+bool finite_state(int64_t n, const float *pm, const float *vel)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const float *p = pm + 4 * i;
+        if (!(std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]) &&
+              std::isfinite(p[3]) && p[3] > 0.f))
+            return false;
+        if (vel) {
+            const float *v = vel + 4 * i;
+            if (!(std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]))) return false;
+        }
+    }
+    return true;
+}
+
+int check_params(double G, double eps, double theta)
+{
+    if (!(G > 0.0) || !std::isfinite(G)) return fail(BH_ERR_INVALID, "G must be finite and > 0");
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(BH_ERR_INVALID, "eps must be finite and >= 0");
+    if (!(theta >= 0.0) || !std::isfinite(theta))
+        return fail(BH_ERR_INVALID, "theta must be finite and >= 0");
+    return BH_OK;
+}
+
+// Particle state of one system: pos, vel, acc, backup pos, backup vel.
+struct SysState {
+    int64_t n = 0;
+    DevBuf mem;
+    double G = 1.0, eps = 0.01, theta = 0.5, dt = 1e-3;
+    float4 *pos() const { return mem.as<float4>(); }
+    float4 *vel() const { return pos() + n; }
+    float4 *acc() const { return pos() + 2 * n; }
+    float4 *bpos() const { return pos() + 3 * n; }
+    float4 *bvel() const { return pos() + 4 * n; }
+    static size_t bytes_for(int64_t n) { return (size_t)n * 5 * sizeof(float4); }
+    int alloc(int64_t nn)
+    {
+        n = nn;
+        return mem.ensure(bytes_for(nn));
+    }
+};
+
+// Copies n x 4 floats (host or device, per flags) into a device array.
+int upload4(float4 *dst, const float *src, int64_t n, unsigned flags, cudaStream_t st)
+{
+    const size_t nb = (size_t)n * sizeof(float4);
+    CKR(cudaMemcpyAsync(dst, src, nb, (flags & BH_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyHostToDevice, st));
+    return BH_OK;
+}
+
+int download4(float *dst, const float4 *src, int64_t n, unsigned flags, cudaStream_t st)
+{
+    const size_t nb = (size_t)n * sizeof(float4);
+    CKR(cudaMemcpyAsync(dst, src, nb, (flags & BH_DEVICE_PTRS) ? cudaMemcpyDeviceToDevice
+                                                               : cudaMemcpyDeviceToHost, st));
+    return BH_OK;
+}
+
+// ------------------------------------------------------- autotune cache
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, bh_tuning> g_tune_cache;
+
+int log2_bucket(int64_t n)
+{
+    int b = 0;
+    while ((1ll << (b + 1)) <= n) ++b;
+    return b;
+}
+
+// ----------------------------------------------------------------- Forest
+
+struct Forest {
+    cudaStream_t st = nullptr;
+    cudaStream_t user = nullptr;
+    cudaEvent_t ev_sync = nullptr;
+    int dev = 0, nsm = 0;
+    unsigned flags = 0;
+    std::vector<SysState *> systems;
+    std::vector<std::unique_ptr<SysState>> owned;
+
+    std::vector<SysStatic> h_sys;
+    std::vector<int4> h_chunks;
+    std::vector<int> h_mode;
+    int n_total = 0, nchunks = 0, nsys = 0;
+    bool tables_dirty = true;
+
+    DevBuf d_sys, d_dyn, d_chunks, d_mode, d_parts, key0, key1, val0, val1, rs_counts, scan_part,
+        spos, ncount, noff, nodeA, nodeB, nlevel, nlist, d_small, d_diag_parts, d_diag_out,
+        d_counts, d_export;
+    unsigned node_cap = 0;
+    struct TileSet {
+        DevBuf buf;
+        int ntiles = 0;
+        bool valid = false;
+    } tiles[3];
+    Small *h_small = nullptr;  // pinned mirror
+
+    bool acc_valid = false;
+    bool tree_valid = false;
+    bh_tuning tune{2, 8, 0, 0};
+
+    cudaGraphExec_t gexec = nullptr;
+    int g_nsteps = -1;
+    unsigned g_cap = 0;
+    bh_tuning g_tune{0, 0, 0, 0};
+    int g_ntotal = -1;
+
+    bool do_walk = true;
+    int64_t last_step_launches = 0;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::array<int, 5>> prof_steps;
+    int64_t launches = 0;
+
+    ~Forest()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        if (ev_sync) cudaEventDestroy(ev_sync);
+        if (h_small) cudaFreeHost(h_small);
+        if (st) cudaStreamDestroy(st);
+    }
+
+    int init(void *user_stream, unsigned fl)
+    {
+        flags = fl;
+        user = (cudaStream_t)user_stream;
+        CKR(cudaGetDevice(&dev));
+        CKR(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        CKR(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        CKR(cudaEventCreateWithFlags(&ev_sync, cudaEventDisableTiming));
+        CKR(cudaMallocHost(&h_small, sizeof(Small)));
+        std::memset(h_small, 0, sizeof(Small));
+        TRY(d_small.ensure(sizeof(Small)));
+        CKR(cudaMemsetAsync(d_small.p, 0, sizeof(Small), st));
+        return BH_OK;
+    }
+
+    // Orders this call's work after everything already queued on the
+    // caller's stream (e.g. tensors the caller just wrote).
+    int begin_call()
+    {
+        CKR(cudaEventRecord(ev_sync, user));
+        CKR(cudaStreamWaitEvent(st, ev_sync, 0));
+        return BH_OK;
+    }
+
+    int sync()
+    {
+        CKR(cudaStreamSynchronize(st));
+        return BH_OK;
+    }
+
+    Small *small() const { return d_small.as<Small>(); }
+
+    BuildBufs bufs() const
+    {
+        BuildBufs b;
+        b.chunks = d_chunks.as<int4>();
+        b.nchunks = nchunks;
+        b.sys = d_sys.as<SysStatic>();
+        b.dyn = d_dyn.as<SysDyn>();
+        b.nsys = nsys;
+        b.mode = d_mode.as<int>();
+        b.parts = d_parts.as<ChunkPart>();
+        b.key0 = key0.as<uint64_t>();
+        b.key1 = key1.as<uint64_t>();
+        b.val0 = val0.as<uint32_t>();
+        b.val1 = val1.as<uint32_t>();
+        b.rs_counts = rs_counts.as<uint32_t>();
+        b.scan_part = scan_part.as<uint32_t>();
+        b.spos = spos.as<float4>();
+        b.ncount = ncount.as<uint32_t>();
+        b.noff = noff.as<uint32_t>();
+        b.nodeA = nodeA.as<float4>();
+        b.nodeB = nodeB.as<int4>();
+        b.nlevel = nlevel.as<uint8_t>();
+        b.nlist = nlist.as<uint32_t>();
+        b.node_cap = node_cap;
+        b.small = small();
+        b.n_total = n_total;
+        b.nsm = nsm;
+        return b;
+    }
+
+    int ensure_nodes(size_t cap)
+    {
+        if (cap <= node_cap && nodeA.p) return BH_OK;
+        TRY(nodeA.ensure(cap * sizeof(float4)));
+        TRY(nodeB.ensure(cap * sizeof(int4)));
+        TRY(nlevel.ensure(cap));
+        TRY(nlist.ensure(cap * sizeof(uint32_t)));
+        node_cap = (unsigned)cap;
+        invalidate_graph();
+        return BH_OK;
+    }
+
+    void invalidate_graph()
+    {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        gexec = nullptr;
+        g_nsteps = -1;
+    }
+
+    // Builds the system / chunk tables from `systems` and sizes the scratch.
+    int setup()
+    {
+        nsys = (int)systems.size();
+        h_sys.assign(nsys, SysStatic{});
+        h_chunks.clear();
+        int64_t start = 0;
+        for (int s = 0; s < nsys; ++s) {
+            SysState *S = systems[s];
+            SysStatic &d = h_sys[s];
+            d.pos = S->pos(); d.vel = S->vel(); d.acc = S->acc(); d.bpos = S->bpos(); d.bvel = S->bvel();
+            d.start = (int)start;
+            d.n = (int)S->n;
+            d.chunk0 = (int)h_chunks.size();
+            for (int64_t c = 0; c < S->n; c += kChunk)
+                h_chunks.push_back(make_int4(s, (int)(start + c), (int)std::min<int64_t>(kChunk, S->n - c), 0));
+            d.nchunk = (int)h_chunks.size() - d.chunk0;
+            d.eps2 = (float)(S->eps * S->eps);
+            d.G = (float)S->G;
+            d.inv_theta2 = S->theta > 0.0 ? (float)(1.0 / (S->theta * S->theta)) : INFINITY;
+            d.half_dt = (float)(0.5 * S->dt);
+            d.dt = (float)S->dt;
+            d.flags = 0;
+            start += S->n;
+            if (start > (int64_t)INT_MAX / 2) return fail(BH_ERR_INVALID, "too many particles (limit 2^30)");
+        }
+        n_total = (int)start;
+        nchunks = (int)h_chunks.size();
+        if (n_total < 1) return fail(BH_ERR_INVALID, "no particles");
+        h_mode.assign(nsys, MODE_KDK);
+        TRY(d_sys.ensure(sizeof(SysStatic) * nsys));
+        TRY(d_dyn.ensure(sizeof(SysDyn) * nsys));
+        TRY(d_mode.ensure(sizeof(int) * nsys));
+        TRY(d_chunks.ensure(sizeof(int4) * nchunks));
+        TRY(d_parts.ensure(sizeof(ChunkPart) * nchunks));
+        TRY(d_diag_parts.ensure(sizeof(DiagPart) * nchunks));
+        TRY(d_diag_out.ensure(sizeof(double) * 8 * nsys));
+        CKR(cudaMemcpyAsync(d_sys.p, h_sys.data(), sizeof(SysStatic) * nsys, cudaMemcpyHostToDevice, st));
+        CKR(cudaMemcpyAsync(d_chunks.p, h_chunks.data(), sizeof(int4) * nchunks, cudaMemcpyHostToDevice, st));
+        CKR(cudaMemcpyAsync(d_mode.p, h_mode.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+        const size_t N = (size_t)n_total;
+        bool moved = false;
+        auto grow = [&](DevBuf &b, size_t nb) -> int {
+            void *old = b.p;
+            int rc = b.ensure(nb);
+            if (b.p != old) moved = true;
+            return rc;
+        };
+        TRY(grow(key0, N * 8));
+        TRY(grow(key1, N * 8));
+        TRY(grow(val0, N * 4));
+        TRY(grow(val1, N * 4));
+        TRY(grow(spos, N * 16));
+        TRY(grow(ncount, (N + 1) * 4));
+        TRY(grow(noff, (N + 1) * 4));
+        const size_t ncounts = (size_t)kRadixBins * nchunks;
+        TRY(grow(rs_counts, ncounts * 4));
+        const size_t scan_n = std::max(ncounts, N + 1);
+        TRY(grow(scan_part, ((scan_n + kScanTile - 1) / kScanTile + 1) * 4));
+        TRY(ensure_nodes(2 * N + 1024));
+        for (auto &t : tiles) t.valid = false;
+        if (moved) invalidate_graph();
+        tables_dirty = false;
+        tree_valid = false;
+        return BH_OK;
+    }
+
+    int upload_sys_table()
+    {
+        CKR(cudaMemcpyAsync(d_sys.p, h_sys.data(), sizeof(SysStatic) * nsys, cudaMemcpyHostToDevice, st));
+        return BH_OK;
+    }
+
+    int set_dt(double dt)
+    {
+        bool changed = false;
+        for (int s = 0; s < nsys; ++s) {
+            const float hd = (float)(0.5 * dt), d = (float)dt;
+            if (h_sys[s].half_dt != hd || h_sys[s].dt != d) changed = true;
+            h_sys[s].half_dt = hd;
+            h_sys[s].dt = d;
+            systems[s]->dt = dt;
+        }
+        if (changed) TRY(upload_sys_table());
+        return BH_OK;
+    }
+
+    int set_modes(const std::vector<int> &m)
+    {
+        if (m == h_mode) return BH_OK;
+        h_mode = m;
+        CKR(cudaMemcpyAsync(d_mode.p, h_mode.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st));
+        // the copy reads pageable memory: make sure it has been consumed
+        CKR(cudaStreamSynchronize(st));
+        return BH_OK;
+    }
+
+    int set_all_modes(int m) { return set_modes(std::vector<int>(nsys, m)); }
+
+    int tile_index(int ppl) const { return ppl == 1 ? 0 : (ppl == 2 ? 1 : 2); }
+
+    int ensure_tiles(int ppl)
+    {
+        TileSet &T = tiles[tile_index(ppl)];
+        if (T.valid) return BH_OK;
+        std::vector<Tile> t;
+        const int sz = 32 * ppl;
+        for (int s = 0; s < nsys; ++s) {
+            const SysStatic &S = h_sys[s];
+            for (int o = 0; o < S.n; o += sz) t.push_back(Tile{S.start + o, std::min(sz, S.n - o), s, 0});
+        }
+        TRY(T.buf.ensure(sizeof(Tile) * t.size()));
+        CKR(cudaMemcpyAsync(T.buf.p, t.data(), sizeof(Tile) * t.size(), cudaMemcpyHostToDevice, st));
+        CKR(cudaStreamSynchronize(st));
+        T.ntiles = (int)t.size();
+        T.valid = true;
+        return BH_OK;
+    }
+
+    WalkArgs walk_args(int ppl, uint32_t *counts) const
+    {
+        WalkArgs a;
+        a.nodeA = nodeA.as<float4>();
+        a.nodeB = nodeB.as<int4>();
+        a.spos = spos.as<float4>();
+        a.sid = val0.as<uint32_t>();
+        a.noff = noff.as<uint32_t>();
+        const TileSet &T = tiles[tile_index(ppl)];
+        a.tiles = T.buf.as<Tile>();
+        a.ntiles = T.ntiles;
+        a.sys = d_sys.as<SysStatic>();
+        a.mode = d_mode.as<int>();
+        a.small = small();
+        a.counts = counts;
+        return a;
+    }
+
+    WalkShape shape() const { return WalkShape{tune.ppl, tune.warps_per_block, tune.blocks_per_sm}; }
+    bool kahan() const { return !(flags & BH_NO_KAHAN); }
+    bool pot() const { return (flags & BH_POTENTIAL) != 0; }
+
+    int mark()
+    {
+        if (!prof) return -1;
+        if (ev_used == ev_pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            ev_pool.push_back(e);
+        }
+        cudaEventRecord(ev_pool[ev_used], st);
+        return (int)ev_used++;
+    }
+
+    void reset_step_counters()
+    {
+        const size_t off = offsetof(Small, queue);
+        const size_t len = offsetof(Small, level_off) - off;
+        cudaMemsetAsync(reinterpret_cast<char *>(small()) + off, 0, len, st);
+    }
+
+    // Enqueues one step (per-system mode from d_mode).
+    int enqueue_step()
+    {
+        TRY(ensure_tiles(tune.ppl));
+        g_launches = 0;
+        const BuildBufs b = bufs();
+        std::array<int, 5> m;
+        reset_step_counters();
+        m[0] = mark();
+        launch_kick_drift_bbox(b, st);
+        m[1] = mark();
+        launch_keys(b, st);
+        launch_sort(b, st);
+        launch_permute(b, st);
+        launch_topology(b, st);
+        launch_com(b, st);
+        m[2] = mark();
+        if (do_walk &&
+            launch_walk(walk_args(tune.ppl, nullptr), shape(), kahan(), pot(), false, nsm, st) < 0)
+            return fail(BH_ERR_INVALID, "unsupported walk shape");
+        m[3] = mark();
+        launch_kick(b, st);
+        m[4] = mark();
+        if (prof) prof_steps.push_back(m);
+        last_step_launches = g_launches;
+        launches += g_launches;
+        CKR(cudaGetLastError());
+        return BH_OK;
+    }
+
+    int read_small()
+    {
+        CKR(cudaMemcpyAsync(h_small, d_small.p, sizeof(Small), cudaMemcpyDeviceToHost, st));
+        CKR(cudaStreamSynchronize(st));
+        return BH_OK;
+    }
+
+    int clear_status()
+    {
+        CKR(cudaMemsetAsync(d_small.p, 0, offsetof(Small, icount), st));
+        return BH_OK;
+    }
+
+    int capture_graph(int nsteps)
+    {
+        invalidate_graph();
+        cudaGraph_t g = nullptr;
+        const bool was_prof = prof;
+        prof = false;
+        CKR(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = BH_OK;
+        for (int k = 0; k < nsteps && rc == BH_OK; ++k) rc = enqueue_step();
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        prof = was_prof;
+        if (rc != BH_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return fail(BH_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            gexec = nullptr;
+            return fail(BH_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+        }
+        g_nsteps = nsteps;
+        g_cap = node_cap;
+        g_tune = tune;
+        g_ntotal = n_total;
+        return BH_OK;
+    }
+
+    // Runs nsteps steps with the current modes; handles node-capacity
+    // overflow by rolling back, growing and retrying.
+    int run(int nsteps, bool graph)
+    {
+        int remaining = nsteps;
+        for (int attempt = 0; remaining > 0; ++attempt) {
+            if (attempt > 8) return fail(BH_ERR_CAPACITY, "node buffer kept overflowing");
+            TRY(clear_status());
+            TRY(ensure_tiles(tune.ppl));
+            if (graph) {
+                walk_max_blocks_per_sm(shape(), kahan(), pot());  // occupancy query outside capture
+                if (!gexec || g_nsteps != remaining || g_cap != node_cap || g_ntotal != n_total ||
+                    std::memcmp(&g_tune, &tune, sizeof tune) != 0)
+                    TRY(capture_graph(remaining));
+                CKR(cudaGraphLaunch(gexec, st));
+                launches += (int64_t)remaining * steps_launches();
+            } else {
+                for (int k = 0; k < remaining; ++k) TRY(enqueue_step());
+            }
+            TRY(read_small());
+            const Small &h = *h_small;
+            if (h.status == ST_OK) {
+                remaining = 0;
+                break;
+            }
+            if (h.status == ST_CAPACITY) {
+                const int done = (int)h.steps_done;
+                launch_restore(bufs(), st);
+                launches += 1;
+                const size_t want = (size_t)h.needed + h.needed / 4 + 1024;
+                TRY(ensure_nodes(want));
+                remaining -= done;
+                tree_valid = false;
+                continue;
+            }
+            if (h.status == ST_WALK_LIMIT)
+                return fail(BH_ERR_CUDA, "walk stopped on a corrupt tree (skip pointer not advancing)");
+            return fail(BH_ERR_CUDA, "device status " + std::to_string(h.status));
+        }
+        tree_valid = true;
+        return BH_OK;
+    }
+
+    // kernels per step, as counted by the launchers when the step was enqueued
+    int64_t steps_launches() const { return last_step_launches; }
+
+    int compute_accel()
+    {
+        TRY(set_all_modes(MODE_ACCEL));
+        TRY(run(1, false));
+        acc_valid = true;
+        return BH_OK;
+    }
+
+    // Tree only (no walk): positions, and so any stored acceleration, unchanged.
+    int build_only()
+    {
+        TRY(set_all_modes(MODE_ACCEL));
+        do_walk = false;
+        const int rc = run(1, false);
+        do_walk = true;
+        return rc;
+    }
+
+    int step(int nsteps, bool graph)
+    {
+        if (!acc_valid) TRY(compute_accel());
+        TRY(set_all_modes(MODE_KDK));
+        return run(nsteps, graph);
+    }
+
+    int ensure_tree()
+    {
+        if (tree_valid) return BH_OK;
+        return compute_accel();
+    }
+
+    int autotune(bh_tuning *best)
+    {
+        double th = 0;
+        for (auto *s : systems) th += s->theta;
+        th /= std::max(1, nsys);
+        const auto key = std::make_tuple(dev, log2_bucket(n_total), (int)std::lround(th * 20), nsys > 1 ? 1 : 0);
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(key);
+            if (it != g_tune_cache.end()) {
+                tune = it->second;
+                if (best) *best = tune;
+                return BH_OK;
+            }
+        }
+        TRY(ensure_tree());
+        const int ppls[3] = {1, 2, 4};
+        const int warps[3] = {4, 8, 16};
+        cudaEvent_t e0, e1;
+        CKR(cudaEventCreate(&e0));
+        CKR(cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        bh_tuning pick = tune;
+        for (int p : ppls) {
+            TRY(ensure_tiles(p));
+            for (int w : warps) {
+                bh_tuning t{p, w, 0, 0};
+                WalkShape sh{p, w, 0};
+                if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0) continue;
+                float ms_best = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    reset_step_counters();
+                    cudaEventRecord(e0, st);
+                    launch_walk(walk_args(p, nullptr), sh, kahan(), pot(), false, nsm, st);
+                    cudaEventRecord(e1, st);
+                    CKR(cudaEventSynchronize(e1));
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0 && ms < ms_best) ms_best = ms;
+                }
+                if (ms_best < best_ms) {
+                    best_ms = ms_best;
+                    pick = t;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        CKR(cudaGetLastError());
+        tune = pick;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_cache[key] = pick;
+        }
+        if (best) *best = pick;
+        return BH_OK;
+    }
+
+    int set_tuning(const bh_tuning *t)
+    {
+        if (!t || (t->ppl != 1 && t->ppl != 2 && t->ppl != 4) || t->warps_per_block < 1 ||
+            t->warps_per_block > 32 || t->blocks_per_sm < 0)
+            return fail(BH_ERR_INVALID, "bad tuning (ppl 1/2/4, warps 1..32, blocks_per_sm >= 0)");
+        WalkShape sh{t->ppl, t->warps_per_block, t->blocks_per_sm};
+        if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0)
+            return fail(BH_ERR_INVALID, "walk shape does not fit on an SM");
+        tune = *t;
+        tune.reserved = 0;
+        return BH_OK;
+    }
+
+    int diagnostics(std::vector<double> &out)
+    {
+        launch_diagnostics(bufs(), d_diag_parts.as<DiagPart>(), d_diag_out.as<double>(), st);
+        launches += 2;
+        out.assign(8 * nsys, 0.0);
+        CKR(cudaMemcpyAsync(out.data(), d_diag_out.p, sizeof(double) * 8 * nsys, cudaMemcpyDeviceToHost, st));
+        TRY(sync());
+        if (!pot())
+            for (int s = 0; s < nsys; ++s) out[8 * s + 1] = NAN;
+        return BH_OK;
+    }
+
+    int interaction_count(int sys, uint32_t *counts, uint64_t *total)
+    {
+        TRY(ensure_tree());
+        TRY(d_counts.ensure(sizeof(uint32_t) * (size_t)n_total));
+        TRY(ensure_tiles(1));
+        TRY(clear_status());
+        reset_step_counters();
+        WalkShape sh{1, 8, 0};
+        launch_walk(walk_args(1, d_counts.as<uint32_t>()), sh, true, false, true, nsm, st);
+        launches += 1;
+        const SysStatic &S = h_sys[sys];
+        std::vector<uint32_t> h((size_t)S.n);
+        CKR(cudaMemcpyAsync(h.data(), d_counts.as<uint32_t>() + S.start, sizeof(uint32_t) * S.n,
+                            cudaMemcpyDeviceToHost, st));
+        TRY(read_small());
+        if (h_small->status != ST_OK) return fail(BH_ERR_CUDA, "counting walk failed");
+        uint64_t t = 0;
+        for (uint32_t c : h) t += c;
+        if (counts) std::memcpy(counts, h.data(), sizeof(uint32_t) * S.n);
+        if (total) *total = t;
+        return BH_OK;
+    }
+
+    int export_tree(int sys, uint64_t *keys, uint32_t *order, bh_node *nodes, float *com_m,
+                    int64_t node_cap_out, int64_t *n_nodes, float *cube)
+    {
+        TRY(ensure_tree());
+        const SysStatic &S = h_sys[sys];
+        uint32_t n01[2];
+        CKR(cudaMemcpyAsync(&n01[0], noff.as<uint32_t>() + S.start, 4, cudaMemcpyDeviceToHost, st));
+        CKR(cudaMemcpyAsync(&n01[1], noff.as<uint32_t>() + S.start + S.n, 4, cudaMemcpyDeviceToHost, st));
+        TRY(sync());
+        const int64_t M = (int64_t)n01[1] - n01[0];
+        if (n_nodes) *n_nodes = M;
+        if ((nodes || com_m) && M > node_cap_out)
+            return fail(BH_ERR_INVALID, "node_cap too small: need " + std::to_string(M));
+        const size_t nb_nodes = sizeof(bh_node) * M, nb_com = sizeof(float4) * M, nb_ord = 4 * (size_t)S.n;
+        TRY(d_export.ensure(nb_nodes + nb_com + nb_ord + 64));
+        char *base = d_export.as<char>();
+        bh_node *dn = reinterpret_cast<bh_node *>(base);
+        float4 *dc = reinterpret_cast<float4 *>(base + ((nb_nodes + 15) & ~size_t(15)));
+        uint32_t *dord = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(dc) + nb_com);
+        launch_export(bufs(), sys, dn, dc, dord, st);
+        launches += 1;
+        if (nodes) CKR(cudaMemcpyAsync(nodes, dn, nb_nodes, cudaMemcpyDeviceToHost, st));
+        if (com_m) CKR(cudaMemcpyAsync(com_m, dc, nb_com, cudaMemcpyDeviceToHost, st));
+        if (order) CKR(cudaMemcpyAsync(order, dord, nb_ord, cudaMemcpyDeviceToHost, st));
+        if (keys) CKR(cudaMemcpyAsync(keys, key0.as<uint64_t>() + S.start, 8 * (size_t)S.n, cudaMemcpyDeviceToHost, st));
+        if (cube) {
+            SysDyn d;
+            CKR(cudaMemcpyAsync(&d, d_dyn.as<SysDyn>() + sys, sizeof d, cudaMemcpyDeviceToHost, st));
+            TRY(sync());
+            cube[0] = d.lo[0]; cube[1] = d.lo[1]; cube[2] = d.lo[2]; cube[3] = d.side;
+        }
+        TRY(sync());
+        return BH_OK;
+    }
+
+    int validate_device()
+    {
+        TRY(clear_status());
+        launch_validate(bufs(), st);
+        launches += 1;
+        TRY(read_small());
+        if (h_small->status == ST_BAD_INPUT) {
+            clear_status();
+            return fail(BH_ERR_INVALID, "non-finite coordinate or non-positive mass in device input");
+        }
+        return BH_OK;
+    }
+
+    int profile_end(double *phase_ms, int64_t *steps, int64_t *nl)
+    {
+        TRY(sync());
+        double ph[BH_NPHASE] = {0, 0, 0};
+        for (auto &m : prof_steps) {
+            float a = 0, b2 = 0, c = 0, d = 0;
+            cudaEventElapsedTime(&a, ev_pool[m[0]], ev_pool[m[1]]);
+            cudaEventElapsedTime(&d, ev_pool[m[3]], ev_pool[m[4]]);
+            cudaEventElapsedTime(&b2, ev_pool[m[1]], ev_pool[m[2]]);
+            cudaEventElapsedTime(&c, ev_pool[m[2]], ev_pool[m[3]]);
+            ph[0] += a + d;
+            ph[1] += b2;
+            ph[2] += c;
+        }
+        if (phase_ms) for (int k = 0; k < BH_NPHASE; ++k) phase_ms[k] = ph[k];
+        if (steps) *steps = (int64_t)prof_steps.size();
+        if (nl) *nl = launches;
+        prof = false;
+        prof_steps.clear();
+        ev_used = 0;
+        return BH_OK;
+    }
+};
+
+}  // namespace
+
+// ======================================================================
+//                               C ABI
+// ======================================================================
+
+struct bh_system {
+    Forest f;
+    bh_params p;
+};
+
+struct bh_forest {
+    Forest f;
+};
+
+extern "C" {
+
+const char *bh_last_error(void) { return g_err.c_str(); }
+
+const char *bh_version(void) { return "bh-gb300 1.0 (sm_103a)"; }
+
+int bh_params_default(bh_params *p)
+{
+    if (!p) return fail(BH_ERR_INVALID, "null params");
+    p->G = 1.0;
+    p->eps = 0.01;
+    p->theta = 0.5;
+    p->max_depth = BH_MAX_DEPTH;
+    p->leaf_cap = 1;
+    p->flags = 0;
+    return BH_OK;
+}
+
+static int check_bh_params(const bh_params *p)
+{
+    if (!p) return fail(BH_ERR_INVALID, "null params");
+    TRY(check_params(p->G, p->eps, p->theta));
+    if (p->max_depth != BH_MAX_DEPTH) return fail(BH_ERR_INVALID, "max_depth must be 21");
+    if (p->leaf_cap != 1) return fail(BH_ERR_INVALID, "leaf_cap must be 1");
+    if (p->flags & ~(BH_POTENTIAL | BH_NO_KAHAN)) return fail(BH_ERR_INVALID, "unknown params flags");
+    return BH_OK;
+}
+
+static int load_state(Forest &f, SysState &S, const float *pm, const float *vel, unsigned flags)
+{
+    if (!(flags & BH_DEVICE_PTRS) && !finite_state(S.n, pm, vel))
+        return fail(BH_ERR_INVALID, "non-finite coordinate or non-positive mass");
+    TRY(upload4(S.pos(), pm, S.n, flags, f.st));
+    if (vel) TRY(upload4(S.vel(), vel, S.n, flags, f.st));
+    else CKR(cudaMemsetAsync(S.vel(), 0, (size_t)S.n * sizeof(float4), f.st));
+    CKR(cudaMemsetAsync(S.acc(), 0, (size_t)S.n * sizeof(float4), f.st));
+    return BH_OK;
+}
+
+int bh_create(bh_system **out, const bh_params *p, int64_t n, const float *pos_mass,
+              const float *vel, void *stream, unsigned flags)
+{
+    if (!out) return fail(BH_ERR_INVALID, "null out");
+    *out = nullptr;
+    TRY(check_bh_params(p));
+    if (n < 1 || n > (1ll << 30)) return fail(BH_ERR_INVALID, "n must be in [1, 2^30]");
+    if (!pos_mass) return fail(BH_ERR_INVALID, "null pos_mass");
+    if (flags & ~BH_DEVICE_PTRS) return fail(BH_ERR_INVALID, "unknown flags");
+    std::unique_ptr<bh_system> s(new (std::nothrow) bh_system);
+    if (!s) return fail(BH_ERR_OOM, "host allocation failed");
+    s->p = *p;
+    Forest &f = s->f;
+    TRY(f.init(stream, p->flags));
+    TRY(f.begin_call());
+    auto st = std::make_unique<SysState>();
+    st->G = p->G; st->eps = p->eps; st->theta = p->theta;
+    TRY(st->alloc(n));
+    TRY(load_state(f, *st, pos_mass, vel, flags));
+    f.systems.push_back(st.get());
+    f.owned.push_back(std::move(st));
+    TRY(f.setup());
+    if (flags & BH_DEVICE_PTRS) TRY(f.validate_device());
+    TRY(f.sync());
+    *out = s.release();
+    return BH_OK;
+}
+
+int bh_destroy(bh_system *s)
+{
+    if (!s) return BH_OK;
+    s->f.sync();
+    delete s;
+    return BH_OK;
+}
+
+int bh_set_state(bh_system *s, const float *pos_mass, const float *vel, unsigned flags)
+{
+    if (!s || !pos_mass) return fail(BH_ERR_INVALID, "null argument");
+    TRY(s->f.begin_call());
+    SysState &S = *s->f.systems[0];
+    if (!(flags & BH_DEVICE_PTRS) && !finite_state(S.n, pos_mass, vel))
+        return fail(BH_ERR_INVALID, "non-finite coordinate or non-positive mass");
+    TRY(upload4(S.pos(), pos_mass, S.n, flags, s->f.st));
+    if (vel) TRY(upload4(S.vel(), vel, S.n, flags, s->f.st));
+    if (flags & BH_DEVICE_PTRS) TRY(s->f.validate_device());
+    s->f.acc_valid = false;
+    s->f.tree_valid = false;
+    return s->f.sync();
+}
+
+int bh_build_tree(bh_system *s)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null system");
+    TRY(s->f.begin_call());
+    return s->f.build_only();
+}
+
+int bh_get_tree(bh_system *s, uint64_t *keys, uint32_t *order, bh_node *nodes, float *com_m,
+                int64_t node_cap, int64_t *n_nodes, float *cube)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null system");
+    TRY(s->f.begin_call());
+    return s->f.export_tree(0, keys, order, nodes, com_m, node_cap, n_nodes, cube);
+}
+
+int bh_compute_accel(bh_system *s, float *acc_out, unsigned flags)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null system");
+    TRY(s->f.begin_call());
+    TRY(s->f.compute_accel());
+    if (acc_out) {
+        TRY(download4(acc_out, s->f.systems[0]->acc(), s->f.systems[0]->n, flags, s->f.st));
+        TRY(s->f.sync());
+    }
+    return BH_OK;
+}
+
+int bh_step(bh_system *s, int nsteps, double dt, int use_graph)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null system");
+    if (nsteps < 0) return fail(BH_ERR_INVALID, "nsteps must be >= 0");
+    if (!std::isfinite(dt)) return fail(BH_ERR_INVALID, "dt must be finite");
+    TRY(s->f.begin_call());
+    TRY(s->f.set_dt(dt));
+    if (nsteps == 0) return s->f.acc_valid ? BH_OK : s->f.compute_accel();
+    return s->f.step(nsteps, use_graph != 0);
+}
+
+int bh_get_state(bh_system *s, float *pos_mass, float *vel, float *acc, unsigned flags)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null system");
+    TRY(s->f.begin_call());
+    SysState &S = *s->f.systems[0];
+    if (pos_mass) TRY(download4(pos_mass, S.pos(), S.n, flags, s->f.st));
+    if (vel) TRY(download4(vel, S.vel(), S.n, flags, s->f.st));
+    if (acc) TRY(download4(acc, S.acc(), S.n, flags, s->f.st));
+    return s->f.sync();
+}
+
+int bh_diagnostics(bh_system *s, double out[8])
+{
+    if (!s || !out) return fail(BH_ERR_INVALID, "null argument");
+    TRY(s->f.begin_call());
+    std::vector<double> v;
+    TRY(s->f.diagnostics(v));
+    std::memcpy(out, v.data(), 8 * sizeof(double));
+    return BH_OK;
+}
+
+int bh_interaction_count(bh_system *s, uint32_t *counts, uint64_t *total)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null system");
+    TRY(s->f.begin_call());
+    return s->f.interaction_count(0, counts, total);
+}
+
+int bh_set_tuning(bh_system *s, const bh_tuning *t)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null system");
+    return s->f.set_tuning(t);
+}
+
+int bh_get_tuning(bh_system *s, bh_tuning *t)
+{
+    if (!s || !t) return fail(BH_ERR_INVALID, "null argument");
+    *t = s->f.tune;
+    return BH_OK;
+}
+
+int bh_autotune(bh_system *s, bh_tuning *best)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null system");
+    TRY(s->f.begin_call());
+    return s->f.autotune(best);
+}
+
+int bh_profile_begin(bh_system *s)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null system");
+    s->f.prof = true;
+    s->f.prof_steps.clear();
+    s->f.ev_used = 0;
+    s->f.launches = 0;
+    return BH_OK;
+}
+
+int bh_profile_end(bh_system *s, double *phase_ms, int64_t *steps, int64_t *launches)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null system");
+    return s->f.profile_end(phase_ms, steps, launches);
+}
+
+// ---------------------------------------------------------------- forest
+
+int bh_forest_create(bh_forest **out, int nsys, const bh_system_desc *d, void *stream,
+                     unsigned flags)
+{
+    if (!out) return fail(BH_ERR_INVALID, "null out");
+    *out = nullptr;
+    if (nsys < 1 || !d) return fail(BH_ERR_INVALID, "need at least one system");
+    if (flags & ~(BH_DEVICE_PTRS | BH_POTENTIAL | BH_NO_KAHAN)) return fail(BH_ERR_INVALID, "unknown flags");
+    for (int s = 0; s < nsys; ++s) {
+        if (d[s].n < 1 || !d[s].pos_mass) return fail(BH_ERR_INVALID, "system " + std::to_string(s) + ": n < 1 or null pos_mass");
+        TRY(check_params(d[s].G, d[s].eps, d[s].theta));
+    }
+    std::unique_ptr<bh_forest> F(new (std::nothrow) bh_forest);
+    if (!F) return fail(BH_ERR_OOM, "host allocation failed");
+    Forest &f = F->f;
+    TRY(f.init(stream, flags & (BH_POTENTIAL | BH_NO_KAHAN)));
+    TRY(f.begin_call());
+    for (int s = 0; s < nsys; ++s) {
+        auto st = std::make_unique<SysState>();
+        st->G = d[s].G; st->eps = d[s].eps; st->theta = d[s].theta; st->dt = d[s].dt;
+        TRY(st->alloc(d[s].n));
+        TRY(load_state(f, *st, d[s].pos_mass, d[s].vel, flags & BH_DEVICE_PTRS));
+        f.systems.push_back(st.get());
+        f.owned.push_back(std::move(st));
+    }
+    TRY(f.setup());
+    if (flags & BH_DEVICE_PTRS) TRY(f.validate_device());
+    TRY(f.sync());
+    *out = F.release();
+    return BH_OK;
+}
+
+int bh_forest_destroy(bh_forest *f)
+{
+    if (!f) return BH_OK;
+    f->f.sync();
+    delete f;
+    return BH_OK;
+}
+
+int bh_forest_compute_accel(bh_forest *f)
+{
+    if (!f) return fail(BH_ERR_INVALID, "null forest");
+    TRY(f->f.begin_call());
+    return f->f.compute_accel();
+}
+
+int bh_forest_step(bh_forest *f, int nsteps, double dt, int use_graph)
+{
+    if (!f) return fail(BH_ERR_INVALID, "null forest");
+    if (nsteps < 0) return fail(BH_ERR_INVALID, "nsteps must be >= 0");
+    TRY(f->f.begin_call());
+    if (dt > 0) TRY(f->f.set_dt(dt));
+    if (nsteps == 0) return f->f.acc_valid ? BH_OK : f->f.compute_accel();
+    return f->f.step(nsteps, use_graph != 0);
+}
+
+int bh_forest_get_state(bh_forest *f, int sys, float *pos_mass, float *vel, float *acc,
+                        unsigned flags)
+{
+    if (!f) return fail(BH_ERR_INVALID, "null forest");
+    if (sys < 0 || sys >= f->f.nsys) return fail(BH_ERR_INVALID, "system index out of range");
+    TRY(f->f.begin_call());
+    SysState &S = *f->f.systems[sys];
+    if (pos_mass) TRY(download4(pos_mass, S.pos(), S.n, flags, f->f.st));
+    if (vel) TRY(download4(vel, S.vel(), S.n, flags, f->f.st));
+    if (acc) TRY(download4(acc, S.acc(), S.n, flags, f->f.st));
+    return f->f.sync();
+}
+
+int bh_forest_set_tuning(bh_forest *f, const bh_tuning *t)
+{
+    if (!f) return fail(BH_ERR_INVALID, "null forest");
+    return f->f.set_tuning(t);
+}
+
+int bh_forest_autotune(bh_forest *f, bh_tuning *best)
+{
+    if (!f) return fail(BH_ERR_INVALID, "null forest");
+    TRY(f->f.begin_call());
+    return f->f.autotune(best);
+}
+
+int bh_forest_info(bh_forest *f, int64_t *n_total, int64_t *n_nodes)
+{
+    if (!f) return fail(BH_ERR_INVALID, "null forest");
+    if (n_total) *n_total = f->f.n_total;
+    if (n_nodes) {
+        TRY(f->f.read_small());
+        *n_nodes = f->f.h_small->M;
+    }
+    return BH_OK;
+}
+
+// ---------------------------------------------------------- micro-benchmarks
+
+int bh_micro_fma_peak(double *gflops, void *stream)
+{
+    if (!gflops) return fail(BH_ERR_INVALID, "null out");
+    *gflops = micro_fma_gflops((cudaStream_t)stream);
+    CKR(cudaGetLastError());
+    return *gflops > 0 ? BH_OK : fail(BH_ERR_CUDA, "fma micro-benchmark failed");
+}
+
+int bh_micro_copy_bw(size_t bytes, double *gbs, void *stream)
+{
+    if (!gbs || bytes < 1024) return fail(BH_ERR_INVALID, "bad argument");
+    *gbs = micro_copy_gbs(bytes, (cudaStream_t)stream);
+    CKR(cudaGetLastError());
+    return *gbs > 0 ? BH_OK : fail(BH_ERR_OOM, "copy micro-benchmark allocation failed");
+}
+
+}  // extern "C"
+
+// ======================================================================
+//                               server
+// ======================================================================
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Job {
+    uint64_t ticket = 0;
+    int64_t n = 0;
+    double G = 1, eps = 0.01, theta = 0.5, dt = 1e-3;
+    int nsteps = 0;
+    std::vector<float> pm, vel;        // inputs, then outputs
+    std::vector<float> acc;
+    double submit_s = 0, admit_s = 0, done_s = 0;
+    int steps_done = 0;
+    int status = BH_OK;
+    bool accel_done = false;
+    size_t bytes = 0;
+    std::unique_ptr<SysState> state;
+};
+
+// Device bytes a resident system needs: its state plus its share of the
+// forest's scratch (keys, ids, sorted copy, counts, ~2 nodes per particle).
+size_t job_bytes(int64_t n)
+{
+    const size_t per = 5 * 16 + (8 + 8 + 4 + 4 + 16 + 4 + 4) + 2 * (16 + 16 + 1 + 4);
+    return (size_t)n * per + 4096 * 64;
+}
+
+}  // namespace
+
+struct bh_server {
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<std::unique_ptr<Job>> pending;
+    std::vector<std::unique_ptr<Job>> resident;
+    std::map<uint64_t, std::unique_ptr<Job>> finished;
+    std::map<uint64_t, int> where;  // 0 pending, 1 resident, 2 finished
+    uint64_t next_ticket = 1;
+    size_t budget = 0;
+    int max_slots = 1;
+    unsigned flags = 0;
+    bool stop = false;
+    size_t resident_bytes = 0;
+    bh_server_stats stats{};
+    Forest forest;
+    std::thread th;
+    Clock::time_point t0;
+    std::string thread_error;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+
+    void loop();
+};
+
+void bh_server::loop()
+{
+    cudaSetDevice(forest.dev);
+    bool dirty = true;
+    for (;;) {
+        std::vector<Job *> admitted;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            while (!stop && pending.empty() && resident.empty()) cv_work.wait(lk);
+            if (stop) break;
+            // FIFO admission by HBM budget and free slot
+            while (!pending.empty() && (int)resident.size() < max_slots &&
+                   resident_bytes + pending.front()->bytes <= budget) {
+                std::unique_ptr<Job> j = std::move(pending.front());
+                pending.pop_front();
+                resident_bytes += j->bytes;
+                j->admit_s = now();
+                where[j->ticket] = 1;
+                admitted.push_back(j.get());
+                resident.push_back(std::move(j));
+                stats.admitted++;
+            }
+            stats.resident_systems = (int64_t)resident.size();
+            stats.peak_resident_systems = std::max(stats.peak_resident_systems, stats.resident_systems);
+            stats.resident_bytes = (int64_t)resident_bytes;
+            stats.peak_resident_bytes = std::max(stats.peak_resident_bytes, stats.resident_bytes);
+        }
+        // allocate and upload outside the lock
+        for (Job *j : admitted) {
+            j->state = std::make_unique<SysState>();
+            SysState &S = *j->state;
+            S.G = j->G; S.eps = j->eps; S.theta = j->theta; S.dt = j->dt;
+            int rc = S.alloc(j->n);
+            if (rc == BH_OK) rc = load_state(forest, S, j->pm.data(), j->vel.empty() ? nullptr : j->vel.data(), 0);
+            if (rc == BH_OK) rc = forest.sync();
+            if (rc != BH_OK) j->status = rc;
+            dirty = true;
+        }
+        const double t_tick0 = now();
+        // drop failed admissions
+        std::vector<Job *> run;
+        for (auto &j : resident)
+            if (j->status == BH_OK) run.push_back(j.get());
+        int rc = BH_OK;
+        if (!run.empty()) {
+            if (dirty) {
+                forest.systems.clear();
+                for (Job *j : run) forest.systems.push_back(j->state.get());
+                rc = forest.setup();
+                dirty = false;
+            }
+            if (rc == BH_OK) {
+                std::vector<int> modes(run.size());
+                for (size_t k = 0; k < run.size(); ++k) modes[k] = run[k]->accel_done ? MODE_KDK : MODE_ACCEL;
+                rc = forest.set_modes(modes);
+                if (rc == BH_OK) rc = forest.run(1, false);
+                if (rc == BH_OK) {
+                    int64_t ps = 0;
+                    for (size_t k = 0; k < run.size(); ++k) {
+                        if (modes[k] == MODE_KDK) {
+                            run[k]->steps_done++;
+                            ps += run[k]->n;
+                        }
+                        run[k]->accel_done = true;
+                    }
+                    stats.ticks++;
+                    stats.particle_steps += ps;
+                }
+            }
+            if (rc != BH_OK)
+                for (Job *j : run) j->status = rc;
+        }
+        // retire finished (or failed) systems
+        std::vector<std::unique_ptr<Job>> done;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            for (size_t k = 0; k < resident.size();) {
+                Job *j = resident[k].get();
+                if (j->status != BH_OK || (j->accel_done && j->steps_done >= j->nsteps)) {
+                    done.push_back(std::move(resident[k]));
+                    resident.erase(resident.begin() + k);
+                    dirty = true;
+                } else {
+                    ++k;
+                }
+            }
+        }
+        for (auto &j : done) {
+            if (j->status == BH_OK && j->state) {
+                SysState &S = *j->state;
+                j->acc.resize((size_t)j->n * 4);
+                j->vel.resize((size_t)j->n * 4);
+                int r2 = download4(j->pm.data(), S.pos(), S.n, 0, forest.st);
+                if (r2 == BH_OK) r2 = download4(j->vel.data(), S.vel(), S.n, 0, forest.st);
+                if (r2 == BH_OK) r2 = download4(j->acc.data(), S.acc(), S.n, 0, forest.st);
+                if (r2 == BH_OK) r2 = forest.sync();
+                if (r2 != BH_OK) j->status = r2;
+            }
+            j->state.reset();
+        }
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stats.busy_s += now() - t_tick0;
+            for (auto &j : done) {
+                resident_bytes -= j->bytes;
+                j->done_s = now();
+                where[j->ticket] = 2;
+                stats.completed++;
+                finished[j->ticket] = std::move(j);
+            }
+            stats.resident_systems = (int64_t)resident.size();
+            stats.resident_bytes = (int64_t)resident_bytes;
+        }
+        if (!done.empty()) cv_done.notify_all();
+    }
+    // shutdown: cancel everything
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &j : pending) {
+        j->status = BH_ERR_CANCELLED;
+        where[j->ticket] = 2;
+        finished[j->ticket] = std::move(j);
+    }
+    pending.clear();
+    for (auto &j : resident) {
+        j->status = BH_ERR_CANCELLED;
+        j->state.reset();
+        where[j->ticket] = 2;
+        finished[j->ticket] = std::move(j);
+    }
+    resident.clear();
+    cv_done.notify_all();
+}
+
+extern "C" {
+
+int bh_server_create(bh_server **out, size_t hbm_budget, int max_slots, void *stream,
+                     unsigned flags)
+{
+    if (!out) return fail(BH_ERR_INVALID, "null out");
+    *out = nullptr;
+    if (max_slots < 1 || hbm_budget < (1u << 20)) return fail(BH_ERR_INVALID, "bad budget or slot count");
+    if (flags & ~(BH_POTENTIAL | BH_NO_KAHAN)) return fail(BH_ERR_INVALID, "unknown flags");
+    std::unique_ptr<bh_server> s(new (std::nothrow) bh_server);
+    if (!s) return fail(BH_ERR_OOM, "host allocation failed");
+    s->budget = hbm_budget;
+    s->max_slots = max_slots;
+    s->flags = flags;
+    TRY(s->forest.init(stream, flags));
+    s->t0 = Clock::now();
+    bh_server *raw = s.get();
+    try {
+        s->th = std::thread([raw] { raw->loop(); });
+    } catch (...) {
+        return fail(BH_ERR_OOM, "could not start the server thread");
+    }
+    *out = s.release();
+    return BH_OK;
+}
+
+int bh_submit(bh_server *s, const bh_request *r, uint64_t *ticket)
+{
+    if (!s || !r || !ticket) return fail(BH_ERR_INVALID, "null argument");
+    if (r->n < 1 || r->n > (1ll << 30) || !r->pos_mass) return fail(BH_ERR_INVALID, "bad request size or null pos_mass");
+    if (r->nsteps < 0) return fail(BH_ERR_INVALID, "nsteps must be >= 0");
+    if (!std::isfinite(r->dt)) return fail(BH_ERR_INVALID, "dt must be finite");
+    TRY(check_params(r->G, r->eps, r->theta));
+    if (!finite_state(r->n, r->pos_mass, r->vel)) return fail(BH_ERR_INVALID, "non-finite coordinate or non-positive mass");
+    auto j = std::make_unique<Job>();
+    j->n = r->n;
+    j->G = r->G; j->eps = r->eps; j->theta = r->theta; j->dt = r->dt;
+    j->nsteps = r->nsteps;
+    j->bytes = job_bytes(r->n);
+    if (j->bytes > s->budget) {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stats.rejected++;
+        return fail(BH_ERR_BUDGET, "request needs " + std::to_string(j->bytes) + " bytes, budget is " + std::to_string(s->budget));
+    }
+    j->pm.assign(r->pos_mass, r->pos_mass + 4 * r->n);
+    if (r->vel) j->vel.assign(r->vel, r->vel + 4 * r->n);
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return fail(BH_ERR_CANCELLED, "server is shutting down");
+    j->ticket = s->next_ticket++;
+    j->submit_s = s->now();
+    *ticket = j->ticket;
+    s->where[j->ticket] = 0;
+    s->pending.push_back(std::move(j));
+    s->stats.submitted++;
+    s->cv_work.notify_one();
+    return BH_OK;
+}
+
+static int take_result(bh_server *s, uint64_t ticket, bh_result *res)
+{
+    // caller holds s->mu
+    auto it = s->finished.find(ticket);
+    Job &j = *it->second;
+    if (res) {
+        res->status = j.status;
+        res->submit_s = j.submit_s;
+        res->admit_s = j.admit_s;
+        res->done_s = j.done_s;
+        res->steps_done = j.steps_done;
+        if (j.status == BH_OK) {
+            const size_t nb = sizeof(float) * 4 * (size_t)j.n;
+            if (res->pos_mass) std::memcpy(res->pos_mass, j.pm.data(), nb);
+            if (res->vel) std::memcpy(res->vel, j.vel.data(), nb);
+            if (res->acc) std::memcpy(res->acc, j.acc.data(), nb);
+        }
+    }
+    const int st = j.status;
+    s->finished.erase(it);
+    s->where.erase(ticket);
+    if (st != BH_OK) return fail(st, "request failed with status " + std::to_string(st));
+    return BH_OK;
+}
+
+int bh_poll(bh_server *s, uint64_t ticket, bh_result *res)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto w = s->where.find(ticket);
+    if (w == s->where.end()) return fail(BH_ERR_INVALID, "unknown ticket");
+    if (w->second != 2) return BH_PENDING;
+    return take_result(s, ticket, res);
+}
+
+int bh_wait(bh_server *s, uint64_t ticket, bh_result *res, double timeout_s)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null server");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto w = s->where.find(ticket);
+    if (w == s->where.end()) return fail(BH_ERR_INVALID, "unknown ticket");
+    const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(std::max(0.0, timeout_s)));
+    while (s->where[ticket] != 2) {
+        if (s->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && s->where[ticket] != 2)
+            return fail(BH_ERR_TIMEOUT, "request not finished within the timeout");
+    }
+    return take_result(s, ticket, res);
+}
+
+int bh_server_stats_get(bh_server *s, bh_server_stats *st)
+{
+    if (!s || !st) return fail(BH_ERR_INVALID, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    *st = s->stats;
+    return BH_OK;
+}
+
+double bh_server_now(bh_server *s) { return s ? s->now() : 0.0; }
+
+int bh_server_destroy(bh_server *s)
+{
+    if (!s) return BH_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->th.joinable()) s->th.join();
+    s->forest.sync();
+    delete s;
+    return BH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,251 @@
+// sort_scan.cu -- segmented LSD radix sort of (63-bit Morton key, 32-bit id)
+// pairs and a device-wide exclusive scan.
+//
+// The sort orders each system's particles by key; it is stable, and keys
+// are produced in input order, so equal keys (coincident points at the depth
+// cap) end up ordered by input index.  Eight passes of 8 bits each; every
+// pass is histogram -> exclusive scan -> stable scatter.  Segmentation costs
+// nothing extra: the per-(chunk, digit) counts are laid out system by system
+// as [system][digit][chunk], so one global exclusive scan yields offsets that
+// already include every earlier system's particles (chunks never straddle
+// systems).  Within a block, ranks come from warp-level __match_any_sync
+// groups: one leader per digit and round updates the warp's running count,
+// so no shared-memory atomics are needed and the order is stable.
+#include "bh.h"
+#include "bh_internal.cuh"
+
+namespace bh {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int kWarps = kChunkThreads / 32;        // 8
+constexpr int kPerWarp = kChunk / kWarps;         // 512
+constexpr int kRounds = kPerWarp / 32;            // 16
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ unsigned count_index(const SysStatic &S, int chunk, int digit)
+{
+    return (unsigned)(kRadixBins * S.chunk0 + digit * S.nchunk + (chunk - S.chunk0));
+}
+
+__global__ void __launch_bounds__(kChunkThreads)
+k_rs_hist(const uint64_t *__restrict__ key, const int4 *__restrict__ chunks,
+          const SysStatic *__restrict__ sys, uint32_t *__restrict__ counts, int shift,
+          const Small *__restrict__ sm)
+{
+    if (sm->status) return;
+    __shared__ uint32_t h[kWarps][kRadixBins];
+    for (int q = threadIdx.x; q < kWarps * kRadixBins; q += blockDim.x) (&h[0][0])[q] = 0;
+    __syncthreads();
+    const int4 c = chunks[blockIdx.x];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int r = 0; r < kRounds; ++r) {
+        const int i = w * kPerWarp + r * 32 + lane;
+        const bool valid = i < c.z;
+        const unsigned d = valid ? (unsigned)((key[c.y + i] >> shift) & (kRadixBins - 1)) : kRadixBins;
+        const unsigned peers = __match_any_sync(FULL, d);
+        if (valid && (peers & lanemask_lt()) == 0) h[w][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    const SysStatic S = sys[c.x];
+    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) {
+        uint32_t t = 0;
+        for (int q = 0; q < kWarps; ++q) t += h[q][d];
+        counts[count_index(S, blockIdx.x, d)] = t;
+    }
+}
+
+__global__ void __launch_bounds__(kChunkThreads)
+k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+             uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+             const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+             const uint32_t *__restrict__ offs, int shift, const Small *__restrict__ sm)
+{
+    if (sm->status) return;
+    __shared__ uint32_t h[kWarps][kRadixBins];
+    __shared__ uint32_t gbase[kRadixBins];
+    for (int q = threadIdx.x; q < kWarps * kRadixBins; q += blockDim.x) (&h[0][0])[q] = 0;
+    __syncthreads();
+    const int4 c = chunks[blockIdx.x];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    uint64_t k[kRounds];
+    uint32_t v[kRounds];
+    uint32_t rd[kRounds];  // (rank within warp << 9) | digit (digit 256 = empty slot)
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const int i = w * kPerWarp + r * 32 + lane;
+        const bool valid = i < c.z;
+        unsigned d = kRadixBins;
+        if (valid) {
+            k[r] = kin[c.y + i];
+            v[r] = vin[c.y + i];
+            d = (unsigned)((k[r] >> shift) & (kRadixBins - 1));
+        }
+        const unsigned peers = __match_any_sync(FULL, d);
+        const unsigned before = valid ? h[w][d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) h[w][d] = before + __popc(peers);
+        __syncwarp();
+        rd[r] = ((before + __popc(peers & lt)) << 9) | d;
+    }
+    __syncthreads();
+    const SysStatic S = sys[c.x];
+    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) {
+        uint32_t run = 0;
+        for (int q = 0; q < kWarps; ++q) {
+            const uint32_t t = h[q][d];
+            h[q][d] = run;
+            run += t;
+        }
+        gbase[d] = offs[count_index(S, blockIdx.x, d)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const unsigned d = rd[r] & 511u;
+        if (d < (unsigned)kRadixBins) {
+            const uint32_t dst = gbase[d] + h[w][d] + (rd[r] >> 9);
+            kout[dst] = k[r];
+            vout[dst] = v[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- scan
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = kScanTile / kScanThreads;  // 8
+
+// Exclusive scan of the block's values (one per thread); returns the
+// exclusive prefix and writes the block total to *total.
+__device__ __forceinline__ uint32_t block_exclusive(uint32_t x, uint32_t *total)
+{
+    __shared__ uint32_t ws[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < nw ? ws[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, s, o);
+            if (lane >= o) s += y;
+        }
+        ws[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    const uint32_t wbase = w ? ws[w - 1] : 0u;
+    const uint32_t tot = ws[nw - 1];
+    __syncthreads();
+    *total = tot;
+    return wbase + inc - x;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_reduce(const uint32_t *__restrict__ in, int n, uint32_t *__restrict__ part,
+              const int *__restrict__ status)
+{
+    if (status && *status) return;
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q)
+        if (base + q < n) s += in[base + q];
+    uint32_t tot;
+    block_exclusive(s, &tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+// Scans part[0..nb) in place (exclusive); *total = sum.
+__global__ void __launch_bounds__(1024)
+k_scan_part(uint32_t *__restrict__ part, int nb, uint32_t *__restrict__ total,
+            const int *__restrict__ status)
+{
+    if (status && *status) return;
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < nb; b0 += 1024 * 4) {
+        const int base = b0 + threadIdx.x * 4;
+        uint32_t x[4], s = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            x[q] = (base + q < nb) ? part[base + q] : 0u;
+            s += x[q];
+        }
+        uint32_t tot;
+        uint32_t e = block_exclusive(s, &tot) + carry;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (base + q < nb) part[base + q] = e;
+            e += x[q];
+        }
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_apply(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n,
+             const uint32_t *__restrict__ part, const int *__restrict__ status)
+{
+    if (status && *status) return;
+    const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    uint32_t x[kScanItems], s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        x[q] = (base + q < n) ? in[base + q] : 0u;
+        s += x[q];
+    }
+    uint32_t tot;
+    uint32_t e = block_exclusive(s, &tot) + part[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        if (base + q < n) out[base + q] = e;
+        e += x[q];
+    }
+}
+
+}  // namespace
+
+void launch_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *partials, uint32_t *total,
+                 const int *status, cudaStream_t st)
+{
+    const int nb = (n + kScanTile - 1) / kScanTile;
+    if (nb == 0) return;
+    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, n, partials, status);
+    k_scan_part<<<1, 1024, 0, st>>>(partials, nb, total, status);
+    k_scan_apply<<<nb, kScanThreads, 0, st>>>(in, out, n, partials, status);
+    g_launches += 3;
+}
+
+void launch_sort(const BuildBufs &b, cudaStream_t st)
+{
+    uint64_t *kin = b.key0, *kout = b.key1;
+    uint32_t *vin = b.val0, *vout = b.val1;
+    const int ncounts = kRadixBins * b.nchunks;
+    for (int pass = 0; pass < kRadixPasses; ++pass) {
+        const int shift = pass * kRadixBits;
+        k_rs_hist<<<b.nchunks, kChunkThreads, 0, st>>>(kin, b.chunks, b.sys, b.rs_counts, shift,
+                                                       b.small);
+        launch_scan(b.rs_counts, b.rs_counts, ncounts, b.scan_part, nullptr, &b.small->status, st);
+        k_rs_scatter<<<b.nchunks, kChunkThreads, 0, st>>>(kin, vin, kout, vout, b.chunks, b.sys,
+                                                          b.rs_counts, shift, b.small);
+        g_launches += 2;
+        uint64_t *tk = kin; kin = kout; kout = tk;
+        uint32_t *tv = vin; vin = vout; vout = tv;
+    }
+}
+
+}  // namespace bh

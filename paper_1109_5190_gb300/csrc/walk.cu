@@ -1,0 +1,246 @@
+// walk.cu -- the Barnes-Hut force walk (the "force computation stage" of
+// Section III, the most computationally intensive part of the method).
+//
+// For each particle i the walk sums, over the cells it accepts and the leaf
+// particles it reaches, G m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2).  A
+// cell of side s at distance d (to its centre of mass) is accepted iff
+// s^2 < theta^2 d^2 (Section III, Fig. 1, with r the cell side); otherwise
+// its children are visited.  The decision is taken per particle, exactly.
+//
+// GPU design (sm_103a, FP32 ALU-bound; no tensor cores: this is not a dense
+// contraction):
+//   * Persistent kernel; each warp pulls tiles of 32*PPL consecutive
+//     Morton-sorted particles from an atomic queue (dynamic load balancing in
+//     place of the paper's runtime work queues, Section III).
+//   * Warp-cooperative traversal: nodes are stored in depth-first pre-order
+//     with a skip pointer (the first node after the subtree).  Each particle
+//     slot keeps the index of the next node it must visit (the root at
+//     first).  The warp votes with __reduce_min_sync for the smallest such
+//     index, loads that node once (a broadcast load shared by all lanes) and
+//     every slot whose next index equals it takes its own decision: accept
+//     (interact, jump to the skip pointer) or open (continue at the next
+//     node, its first child).  The vote replaces an explicit per-warp
+//     (node, lane-mask) stack: the set of slots waiting on a node is exactly
+//     the lane mask such a stack would carry, no stack can overflow, and the
+//     warp visits the union of its particles' traversals in memory order.
+//   * One-particle leaves carry threshold -1 (always accepted as the particle
+//     itself); depth-cap buckets carry -2 and are summed particle by
+//     particle (a warp-uniform branch).
+//   * Compensated (Kahan) FP32 accumulation of each force component (and of
+//     the potential when requested).
+//   * The loop's trip count is bounded by the node count: every iteration
+//     strictly increases the smallest next index.  A skip pointer that does
+//     not move forward means a corrupt tree; the warp then stops and reports
+//     ST_WALK_LIMIT instead of spinning.
+#include "bh.h"
+#include "bh_internal.cuh"
+
+namespace bh {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <bool KAHAN>
+__device__ __forceinline__ void acc_add(float &s, float &c, float x)
+{
+    if (KAHAN) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    } else {
+        s += x;
+    }
+}
+
+template <int PPL, bool KAHAN, bool POT, bool COUNT>
+__global__ void k_walk(WalkArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    Small *sm = a.small;
+    if (sm->status) return;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(&sm->queue, 1u);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= a.ntiles) break;
+        const Tile tl = a.tiles[t];
+        const SysStatic &S = a.sys[tl.sys];
+        const int sstart = S.start;
+        const int root = (int)a.noff[sstart];
+        const int nend = (int)a.noff[sstart + S.n];
+        const float eps2 = S.eps2;
+
+        float px[PPL], py[PPL], pz[PPL];
+        int nxt[PPL], myj[PPL];
+        float ax[PPL], ay[PPL], az[PPL], cx[PPL], cy[PPL], cz[PPL], pp[PPL], cp[PPL];
+        unsigned cnt[PPL];
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+            const int o = k * 32 + lane;
+            myj[k] = tl.start + o;
+            ax[k] = ay[k] = az[k] = cx[k] = cy[k] = cz[k] = pp[k] = cp[k] = 0.f;
+            cnt[k] = 0;
+            if (o < tl.count) {
+                const float4 P = a.spos[myj[k]];
+                px[k] = P.x; py[k] = P.y; pz[k] = P.z;
+                nxt[k] = root;
+            } else {
+                px[k] = py[k] = pz[k] = 0.f;
+                nxt[k] = nend;
+            }
+        }
+
+        for (;;) {
+            int m = nxt[0];
+#pragma unroll
+            for (int k = 1; k < PPL; ++k) m = min(m, nxt[k]);
+            const int cur = (int)__reduce_min_sync(FULL, (unsigned)m);
+            if (cur >= nend) break;
+            const float4 A = __ldg(&a.nodeA[cur]);
+            const int4 B = __ldg(&a.nodeB[cur]);
+            if (B.x <= cur) {  // corrupt skip pointer: report, never spin
+                if (lane == 0) atomicExch(&sm->status, ST_WALK_LIMIT);
+                break;
+            }
+            const float crit = __int_as_float(B.y);
+            if (crit == kBucketCrit) {
+                for (int q = B.z; q < B.z + B.w; ++q) {
+                    const float4 P = __ldg(&a.spos[q]);
+#pragma unroll
+                    for (int k = 0; k < PPL; ++k) {
+                        if (nxt[k] == cur) {
+                            const float dx = P.x - px[k], dy = P.y - py[k], dz = P.z - pz[k];
+                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+                            const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                            const float mi = P.w * inv;
+                            const float mi3 = mi * inv * inv;
+                            acc_add<KAHAN>(ax[k], cx[k], mi3 * dx);
+                            acc_add<KAHAN>(ay[k], cy[k], mi3 * dy);
+                            acc_add<KAHAN>(az[k], cz[k], mi3 * dz);
+                            if (POT && q != myj[k]) acc_add<KAHAN>(pp[k], cp[k], mi);
+                            if (COUNT) cnt[k] += 1;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < PPL; ++k)
+                    if (nxt[k] == cur) nxt[k] = B.x;
+            } else {
+#pragma unroll
+                for (int k = 0; k < PPL; ++k) {
+                    if (nxt[k] == cur) {
+                        const float dx = A.x - px[k], dy = A.y - py[k], dz = A.z - pz[k];
+                        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                        if (d2 > crit) {
+                            const float r2 = d2 + eps2;
+                            const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                            const float mi = A.w * inv;
+                            const float mi3 = mi * inv * inv;
+                            acc_add<KAHAN>(ax[k], cx[k], mi3 * dx);
+                            acc_add<KAHAN>(ay[k], cy[k], mi3 * dy);
+                            acc_add<KAHAN>(az[k], cz[k], mi3 * dz);
+                            if (POT && !(crit == kLeafCrit && B.z == myj[k]))
+                                acc_add<KAHAN>(pp[k], cp[k], mi);
+                            if (COUNT) cnt[k] += 1;
+                            nxt[k] = B.x;
+                        } else {
+                            nxt[k] = cur + 1;
+                        }
+                    }
+                }
+            }
+        }
+
+        const float G = S.G;
+        float4 *acc = S.acc;
+#pragma unroll
+        for (int k = 0; k < PPL; ++k) {
+            const int o = k * 32 + lane;
+            if (o < tl.count) {
+                const uint32_t v = a.sid[myj[k]];
+                if (COUNT) a.counts[v] = cnt[k];
+                else acc[(int)v - sstart] = make_float4(G * ax[k], G * ay[k], G * az[k],
+                                                        POT ? -G * pp[k] : 0.f);
+            }
+        }
+    }
+}
+
+// Blocks of `warps` warps that fit on one SM, queried once per variant and
+// block size (never during stream capture: callers query before capturing).
+template <int PPL, bool KAHAN, bool POT, bool COUNT>
+int occupancy(int warps)
+{
+    static int cache[33] = {0};
+    if (warps < 1 || warps > 32) return 0;
+    if (cache[warps] == 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk<PPL, KAHAN, POT, COUNT>,
+                                                          warps * 32, 0) != cudaSuccess)
+            occ = 0;
+        cache[warps] = occ > 0 ? occ : -1;
+    }
+    return cache[warps] > 0 ? cache[warps] : 0;
+}
+
+template <int PPL, bool KAHAN, bool POT, bool COUNT>
+void launch_one(const WalkArgs &a, const WalkShape &sh, int nsm, cudaStream_t st)
+{
+    const int threads = sh.warps * 32;
+    int bps = sh.blocks_per_sm;
+    if (bps <= 0) bps = occupancy<PPL, KAHAN, POT, COUNT>(sh.warps);
+    if (bps <= 0) bps = 1;
+    k_walk<PPL, KAHAN, POT, COUNT><<<nsm * bps, threads, 0, st>>>(a);
+}
+
+}  // namespace
+
+int launch_walk(const WalkArgs &a, const WalkShape &sh, bool kahan, bool pot, bool count,
+                int nsm, cudaStream_t st)
+{
+    if (count) {
+        launch_one<1, true, false, true>(a, sh, nsm, st);
+        g_launches += 1;
+        return 1;
+    }
+#define BH_WALK_CASE(P)                                                         \
+    case P:                                                                     \
+        if (kahan) {                                                            \
+            if (pot) launch_one<P, true, true, false>(a, sh, nsm, st);          \
+            else launch_one<P, true, false, false>(a, sh, nsm, st);             \
+        } else {                                                                \
+            if (pot) launch_one<P, false, true, false>(a, sh, nsm, st);         \
+            else launch_one<P, false, false, false>(a, sh, nsm, st);            \
+        }                                                                       \
+        break;
+    switch (sh.ppl) {
+        BH_WALK_CASE(1)
+        BH_WALK_CASE(2)
+        BH_WALK_CASE(4)
+        default: return -1;
+    }
+#undef BH_WALK_CASE
+    g_launches += 1;
+    return 1;
+}
+
+int walk_max_blocks_per_sm(const WalkShape &sh, bool kahan, bool pot)
+{
+    occupancy<1, true, false, true>(8);  // the counting variant's shape
+#define BH_OCC_CASE(P)                                                          \
+    case P:                                                                     \
+        if (kahan) return pot ? occupancy<P, true, true, false>(sh.warps)       \
+                              : occupancy<P, true, false, false>(sh.warps);     \
+        return pot ? occupancy<P, false, true, false>(sh.warps)                \
+                   : occupancy<P, false, false, false>(sh.warps);
+    switch (sh.ppl) {
+        BH_OCC_CASE(1)
+        BH_OCC_CASE(2)
+        BH_OCC_CASE(4)
+        default: return 0;
+    }
+#undef BH_OCC_CASE
+}
+
+}  // namespace bh

@@ -1,0 +1,347 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Gates: Morton keys, sort order and node topology bit-exact; per-particle
+accelerations within p99 <= 1e-5 and max <= 1e-3 relative (see metrics.py);
+per-particle interaction counts equal except for opening-test ties.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from metrics import accel_errors, assert_accel_close
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1109_5190_gb300 import binding as B  # noqa: E402
+
+
+def make(pm, vel=None, eps=0.01, theta=0.5, G=1.0, flags=0):
+    return B.bh_create(B.params(G, eps, theta, flags), np.ascontiguousarray(pm, np.float32),
+                       None if vel is None else np.ascontiguousarray(vel, np.float32))
+
+
+def gpu_accel(h, n):
+    out = np.zeros((n, 4), np.float32)
+    B.bh_compute_accel(h, out)
+    return out
+
+
+def oracle_nodes(T):
+    nd = T.nodes()
+    return nd
+
+
+def check_tree(h, pm):
+    n = len(pm)
+    g = B.bh_get_tree(h, n)
+    T = oracle.Tree(pm)
+    order, keys = T.order()
+    assert np.array_equal(g["order"].astype(np.int64), order), "sort order"
+    assert np.array_equal(g["keys"], keys[order]), "sorted keys"
+    lo, side = T.cube()
+    assert np.array_equal(g["cube"][:3], lo) and g["cube"][3] == side, "key cube"
+    nd = T.nodes()
+    gn = g["nodes"]
+    assert len(gn) == T.m, f"node count {len(gn)} vs {T.m}"
+    assert np.array_equal(gn["level"].astype(np.int64), nd["level"])
+    assert np.array_equal(gn["prefix"], nd["prefix"])
+    assert np.array_equal(gn["first"].astype(np.int64), nd["first"])
+    assert np.array_equal(gn["count"].astype(np.int64), nd["count"])
+    assert np.array_equal(gn["childmask"].astype(np.int64), nd["childmask"])
+    # centres of mass: FP32 vs FP64, relative to the system size
+    com = g["com_m"].astype(np.float64)
+    assert np.allclose(com[:, 3], nd["mass"], rtol=2e-6, atol=0)
+    scale = max(float(side), 1e-30)
+    assert np.abs(com[:, :3] - nd["com"]).max() <= 2e-6 * (scale + np.abs(nd["com"]).max())
+    return T
+
+
+CASES = [
+    ("plummer", 4096, 1), ("plummer", 4097, 2), ("uniform", 5000, 3), ("gauss", 1, 4),
+    ("gauss", 2, 5), ("gauss", 33, 6), ("clustered", 3000, 7), ("planar", 2000, 8),
+    ("line", 777, 9), ("dups", 1000, 10), ("equal", 100, 11),
+]
+
+
+def gen(kind, n, seed):
+    if kind == "plummer":
+        return synth.plummer(n, seed)
+    if kind == "uniform":
+        return synth.uniform_cube(n, seed)
+    if kind == "dups":
+        pm, v = synth.random_cloud(n, seed, "gauss")
+        pm[100:140, :3] = pm[99, :3]
+        pm[500:503, :3] = pm[7, :3]
+        return pm, v
+    if kind == "equal":
+        pm, v = synth.random_cloud(n, seed, "gauss")
+        pm[:, :3] = pm[0, :3]
+        return pm, v
+    return synth.random_cloud(n, seed, kind)
+
+
+@pytest.mark.parametrize("kind,n,seed", CASES)
+def test_tree_bit_exact_and_accel(kind, n, seed):
+    pm, vel = gen(kind, n, seed)
+    theta, eps = 0.5, 0.01
+    h = make(pm, vel, eps, theta)
+    try:
+        a = gpu_accel(h, n)
+        T = check_tree(h, pm)
+        ref, _, cnt = T.accel(theta, eps)
+        assert_accel_close(a, ref, what=f"{kind} n={n}")
+        gc, tot = B.bh_interaction_count(h, n)
+        mism = np.count_nonzero(gc.astype(np.int64) != cnt)
+        assert mism <= max(2, n // 1000), f"{mism} interaction-count mismatches"
+    finally:
+        B.bh_destroy(h)
+
+
+def test_theta_zero_matches_direct_sum():
+    pm, _ = synth.plummer(4096, 12)
+    h = make(pm, eps=0.01, theta=0.0)
+    try:
+        a = gpu_accel(h, 4096)
+        ref, _ = oracle.direct(pm, 0.01)
+        assert_accel_close(a, ref, what="theta=0 vs direct")
+        _, tot = B.bh_interaction_count(h, 4096)
+        assert tot == 4096 * 4096
+    finally:
+        B.bh_destroy(h)
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.7, 0.8, 1.0])
+def test_other_theta(theta):
+    pm, _ = synth.uniform_cube(8192, 13)
+    h = make(pm, eps=0.005, theta=theta)
+    try:
+        a = gpu_accel(h, 8192)
+        ref, _, _ = oracle.Tree(pm).accel(theta, 0.005)
+        assert_accel_close(a, ref, what=f"theta={theta}")
+    finally:
+        B.bh_destroy(h)
+
+
+def test_kepler_two_body_closed_form():
+    pm, vel, k = synth.kepler_pair(0.6, 0.4, 1.0, 0.5)
+    h = make(pm, vel, eps=0.0, theta=0.5)
+    try:
+        a = gpu_accel(h, 2)[:, :3].astype(np.float64)
+        x = pm[:, :3].astype(np.float64)
+        r = x[1] - x[0]
+        rr = np.linalg.norm(r)
+        np.testing.assert_allclose(a[0], 0.4 * r / rr ** 3, rtol=1e-6)
+        np.testing.assert_allclose(a[1], -0.6 * r / rr ** 3, rtol=1e-6)
+    finally:
+        B.bh_destroy(h)
+
+
+def test_potential_and_diagnostics():
+    pm, vel = synth.plummer(4096, 14)
+    h = make(pm, vel, eps=0.01, theta=0.5, flags=B.BH_POTENTIAL)
+    try:
+        a = gpu_accel(h, 4096)
+        ref, pot, _ = oracle.Tree(pm).accel(0.5, 0.01)
+        assert_accel_close(a, ref)
+        e = np.abs(a[:, 3] - pot) / np.abs(pot)
+        assert np.percentile(e, 99) <= 1e-5 and e.max() <= 1e-4
+        d = B.bh_diagnostics(h)
+        dref = oracle.diagnostics(pm, vel, a[:, 3].astype(np.float64))
+        np.testing.assert_allclose(d, dref, rtol=1e-12, atol=1e-15)
+    finally:
+        B.bh_destroy(h)
+
+
+def test_leapfrog_steps_against_oracle():
+    # one force evaluation plus 10 KDK steps, dt = 1e-3 (Plummer N = 4096);
+    # every step's tree and forces are checked from the GPU's own positions
+    pm, vel = synth.plummer(4096, 1)
+    eps, theta, dt = 0.01, 0.5, 1e-3
+    h = make(pm, vel, eps, theta)
+    try:
+        x = pm.copy()
+        v = vel.copy()
+        a = gpu_accel(h, 4096)
+        for step in range(10):
+            B.bh_step(h, 1, dt)
+            x1 = np.zeros_like(x); v1 = np.zeros_like(v); a1 = np.zeros_like(a)
+            B.bh_get_state(h, x1, v1, a1)
+            # the step itself: FP64 KDK from the GPU's previous state
+            vh = v[:, :3].astype(np.float64) + 0.5 * dt * a[:, :3]
+            xe = x[:, :3].astype(np.float64) + dt * vh
+            assert np.abs(x1[:, :3] - xe).max() <= 4e-7 * (1 + np.abs(xe).max())
+            check_tree(h, x1)
+            ref, _, _ = oracle.Tree(x1).accel(theta, eps)
+            assert_accel_close(a1, ref, what=f"step {step}")
+            ve = vh + 0.5 * dt * a1[:, :3].astype(np.float64)
+            assert np.abs(v1[:, :3] - ve).max() <= 4e-7 * (1 + np.abs(ve).max())
+            x, v, a = x1, v1, a1
+    finally:
+        B.bh_destroy(h)
+
+
+def test_graph_mode_matches_plain_mode():
+    pm, vel = synth.plummer(8192, 15)
+    outs = []
+    for graph in (False, True):
+        h = make(pm, vel)
+        try:
+            B.bh_step(h, 5, 1e-3, use_graph=graph)
+            x = np.zeros_like(pm); a = np.zeros_like(pm)
+            B.bh_get_state(h, x, None, a)
+            outs.append((x, a))
+        finally:
+            B.bh_destroy(h)
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_launch_shape_does_not_change_results():
+    pm, _ = synth.uniform_cube(20000, 16)
+    h = make(pm, eps=0.005, theta=0.6)
+    try:
+        ref = None
+        for ppl in (1, 2, 4):
+            for w in (4, 8, 16):
+                B.bh_set_tuning(h, ppl, w, 0)
+                a = gpu_accel(h, 20000)
+                if ref is None:
+                    ref = a
+                assert np.array_equal(a, ref), (ppl, w)
+        best = B.bh_autotune(h)
+        assert best[0] in (1, 2, 4)
+        assert np.array_equal(gpu_accel(h, 20000), ref)
+    finally:
+        B.bh_destroy(h)
+
+
+def test_node_capacity_overflow_is_recovered():
+    # 2048 tight pairs: every pair hangs a chain of ~17 single-child cells, so
+    # the tree has ~9 nodes per particle, far above the initial capacity of
+    # 2n + 1024: the build reports the overflow, the buffers grow, and the
+    # step is redone -- both for a force evaluation and inside KDK steps.
+    rng = np.random.default_rng(17)
+    c = rng.uniform(-1, 1, (2048, 3))
+    pts = np.concatenate([c, c + rng.normal(0, 1e-6, c.shape)])
+    pm = np.zeros((4096, 4), np.float32)
+    pm[:, :3] = pts
+    pm[:, 3] = 1.0 / 4096
+    vel = np.zeros_like(pm)
+    vel[:, :3] = rng.normal(0, 0.1, (4096, 3))
+    h = make(pm, vel, eps=0.01, theta=0.5)
+    try:
+        a = gpu_accel(h, 4096)
+        T = check_tree(h, pm)
+        assert T.m > 2 * 4096 + 1024
+        ref, _, _ = T.accel(0.5, 0.01)
+        assert_accel_close(a, ref)
+        B.bh_step(h, 3, 1e-3)
+        x = np.zeros_like(pm); a = np.zeros_like(pm)
+        B.bh_get_state(h, x, None, a)
+        assert_accel_close(a, oracle.Tree(x).accel(0.5, 0.01)[0])
+    finally:
+        B.bh_destroy(h)
+
+
+def test_device_pointers_and_torch_stream():
+    pm, vel = synth.plummer(3000, 18)
+    d_pm = torch.from_numpy(pm).cuda()
+    d_vel = torch.from_numpy(vel).cuda()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        h = B.bh_create(B.params(1.0, 0.01, 0.5), d_pm, d_vel, s)
+        try:
+            out = torch.zeros_like(d_pm)
+            B.bh_compute_accel(h, out)
+            s.synchronize()
+            ref, _, _ = oracle.Tree(pm).accel(0.5, 0.01)
+            assert_accel_close(out.cpu().numpy(), ref)
+        finally:
+            B.bh_destroy(h)
+    bad = d_pm.clone()
+    bad[5, 3] = 0.0  # zero mass is rejected on the device
+    with pytest.raises(B.BHError):
+        B.bh_create(B.params(), bad, d_vel)
+
+
+def test_forest_systems_equal_alone():
+    systems = synth.forest_systems(12, 256, 6000, seed=19, theta=0.5, eps=0.01)
+    descs = [dict(pos_mass=s.pos_mass, vel=s.vel, eps=s.eps, theta=s.theta, dt=1e-3) for s in systems]
+    # give two systems other parameters: per-system theta / eps / G
+    descs[3]["theta"] = 0.8
+    descs[5]["eps"] = 0.002
+    descs[7]["G"] = 2.5
+    f = B.bh_forest_create(descs)
+    try:
+        B.bh_forest_compute_accel(f)
+        B.bh_forest_step(f, 3, 1e-3, use_graph=True)
+        for k, d in enumerate(descs):
+            n = len(d["pos_mass"])
+            xf = np.zeros((n, 4), np.float32); af = np.zeros((n, 4), np.float32)
+            B.bh_forest_get_state(f, k, xf, None, af)
+            h = make(d["pos_mass"], d["vel"], d["eps"], d["theta"], d.get("G", 1.0))
+            try:
+                B.bh_step(h, 3, 1e-3)
+                x1 = np.zeros_like(xf); a1 = np.zeros_like(af)
+                B.bh_get_state(h, x1, None, a1)
+            finally:
+                B.bh_destroy(h)
+            assert np.array_equal(xf, x1) and np.array_equal(af, a1), f"system {k}"
+        ref, _, _ = oracle.Tree(xf).accel(descs[-1]["theta"], descs[-1]["eps"])
+        assert_accel_close(af, ref)
+    finally:
+        B.bh_forest_destroy(f)
+
+
+def test_server_results_same_alone_and_in_mix():
+    reqs = []
+    for k in range(10):
+        pm, vel = (synth.plummer if k % 2 else synth.uniform_cube)(1500 + 700 * k, 100 + k)
+        reqs.append(dict(pos_mass=pm, vel=vel, theta=0.5 + 0.03 * k, eps=0.01, dt=1e-3,
+                         nsteps=3 + (k % 4)))
+    srv = B.bh_server_create(8 << 30, 6)
+    try:
+        tickets = [B.bh_submit(srv, r["pos_mass"], r["vel"], 1.0, r["eps"], r["theta"], r["dt"],
+                               r["nsteps"]) for r in reqs]
+        res = [B.bh_wait(srv, t, len(r["pos_mass"]), 120.0) for t, r in zip(tickets, reqs)]
+        st = B.bh_server_stats_get(srv)
+        assert st["completed"] == 10 and st["peak_resident_systems"] > 1
+    finally:
+        B.bh_server_destroy(srv)
+    for r, out in zip(reqs, res):
+        assert out["status"] == 0 and out["steps_done"] == r["nsteps"]
+        h = make(r["pos_mass"], r["vel"], r["eps"], r["theta"])
+        try:
+            B.bh_step(h, r["nsteps"], r["dt"])
+            x = np.zeros_like(r["pos_mass"]); a = np.zeros_like(x)
+            B.bh_get_state(h, x, None, a)
+        finally:
+            B.bh_destroy(h)
+        assert np.array_equal(out["pos_mass"], x) and np.array_equal(out["acc"], a)
+
+
+def test_uniform_cube_million_step0_all_particles():
+    # uniform cube N = 2^20, eps = 0.005, theta in {0.5, 0.7}: every particle
+    # against the oracle at step 0, then a seeded 4096 sample after 2 steps
+    n = 1 << 20
+    pm, vel = synth.uniform_cube(n, 2)
+    for theta in (0.5, 0.7):
+        h = make(pm, vel, eps=0.005, theta=theta)
+        try:
+            a = gpu_accel(h, n)
+            T = oracle.Tree(pm)
+            ref, _, _ = T.accel(theta, 0.005)
+            assert_accel_close(a, ref, what=f"C2 theta={theta}")
+            B.bh_step(h, 2, 5e-4)
+            x = np.zeros_like(pm); a = np.zeros_like(pm)
+            B.bh_get_state(h, x, None, a)
+            idx = np.random.default_rng(20).choice(n, 4096, replace=False)
+            ref, _, _ = oracle.Tree(x).accel(theta, 0.005, targets=idx)
+            assert_accel_close(a[idx], ref, what=f"C2 step 2 theta={theta}")
+        finally:
+            B.bh_destroy(h)

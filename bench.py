@@ -1,0 +1,310 @@
+#!/usr/bin/env python3
+"""Benchmark: Barnes-Hut particle-steps/s on one GB300 (or N replicas).
+
+Default workload (one "step" = one kick-drift-kick leapfrog step, i.e. one
+pass of the whole hot path: bounding box, Morton keys, radix sort, octree
+topology, centre-of-mass pass, walk, kicks): a uniform cube of N = 1,048,576
+particles U[-1,1]^3, zero velocities, masses 1/N, G = 1, eps = 0.005,
+theta = 0.5, dt = 5e-4, FP32 walk with FP64 root reductions, seed 2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Device time comes from CUDA events the library records
+on its own stream around each phase of each step (integrate, build, walk); L2
+is flushed between timed steps (outside the timed events).  For N > 1 (launched
+by torch.distributed.run) every rank runs an independent replica; the value is
+the particle-steps of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Barnes-Hut particle-steps/s batched vs plain at force err≤1e-4; p50/p99 latency"
+UNIT = "particle-steps/s"
+WORKLOAD = ("uniform cube N=1,048,576 U[-1,1]^3, v=0, m=1/N, G=1, eps=0.005, theta=0.5, "
+            "dt=5e-4 KDK leapfrog, FP32 walk (Kahan) + FP64 root reductions, seed 2")
+N_PART = 1 << 20
+THETA, EPS, DT, SEED = 0.5, 0.005, 5e-4, 2
+FLOPS_PER_INTERACTION = 20
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- reference
+
+def cpu_sample(pm, sample: int, seed: int = 7):
+    """Oracle (FP64 CPU Barnes-Hut) on a bounded sample of one step: the full
+    tree build plus the walk of `sample` particles, extrapolated to all N.
+    Returns (particle-steps/s, seconds spent, threads)."""
+    import numpy as np
+    import oracle
+    n = len(pm)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    T = oracle.Tree(pm)
+    t1 = time.perf_counter()
+    idx = np.random.default_rng(seed).choice(n, min(sample, n), replace=False)
+    T.accel(THETA, EPS, targets=idx, nthreads=threads)
+    t2 = time.perf_counter()
+    t_step = (t1 - t0) + (t2 - t1) * n / len(idx)
+    return n / t_step, t2 - t0, threads
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    pm, _ = synth.uniform_cube(N_PART, SEED)
+    sample = args.ref_sample
+    vals, spent = [], 0.0
+    for k in range(args.warmup + args.steps):
+        v, s, threads = cpu_sample(pm, sample, seed=100 + k)
+        spent += s
+        if k >= args.warmup:
+            vals.append(v)
+    value = len(vals) / sum(1.0 / v for v in vals)  # total particle-steps / total time
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * N_PART / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_PART},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"each step: full FP64 tree build of all {N_PART} particles "
+                                   f"+ walk of {sample} random particles, extrapolated to N"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------- GPU
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1109_5190_gb300 import binding as B
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    pm, vel = synth.uniform_cube(N_PART, SEED)
+    d_pm = torch.from_numpy(pm).to(dev)
+    d_vel = torch.from_numpy(vel).to(dev)
+    h = B.bh_create(B.params(1.0, EPS, THETA), d_pm, d_vel, stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    if args.ppl:
+        B.bh_set_tuning(h, args.ppl, args.warps, 0)
+        tuning = B.bh_get_tuning(h)
+    else:
+        tuning = B.bh_autotune(h)
+    B.bh_compute_accel(h)
+    for _ in range(args.warmup):
+        B.bh_step(h, 1, DT)
+    ws0 = B.bh_walk_stats(h)
+    inter0 = ws0["interactions"]
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    B.bh_profile_begin(h)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        B.bh_step(h, 1, DT)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    phase_ms, nsteps, launches = B.bh_profile_end(h)
+    clocks = sampler.stop()
+    ws1 = B.bh_walk_stats(h)
+    inter1 = ws1["interactions"]
+    dev_ms = float(phase_ms.sum())
+
+    t_max = dev_ms
+    if ws > 1:
+        tt = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = ws * N_PART * args.steps / (t_max * 1e-3)
+
+    # ---- roofline of the dominant kernel (the walk): FP32 ALU bound
+    walk_ms = phase_ms[2] / nsteps
+    inter = 0.5 * (inter0 + inter1)
+    achieved = inter * FLOPS_PER_INTERACTION / (walk_ms * 1e-3) / 1e12
+    fma_peak = B.bh_micro_fma_peak(stream) / 1e3
+    peaks, peak_src = measured_peaks()
+    build_ms = phase_ms[1] / nsteps
+    # algorithmic bytes of the build: 144 B per particle + 48 B per node
+    n_nodes = B.bh_node_count(h)
+    build_bytes = 144 * N_PART + 48 * n_nodes
+    build_gbs = build_bytes / (build_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hpm = torch.empty((N_PART, 4), dtype=torch.float32, pin_memory=True).numpy()
+        hvel = torch.empty_like(torch.from_numpy(hpm)).pin_memory().numpy()
+        hacc = torch.empty_like(torch.from_numpy(hpm)).pin_memory().numpy()
+        B.bh_get_state(h, hpm, hvel, hacc)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            B.bh_set_state(h, hpm, hvel, hacc)
+            B.bh_step(h, 1, DT)
+            B.bh_get_state(h, hpm, hvel, hacc)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": N_PART * args.steps * ws / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * N_PART * 16, "d2h_bytes_per_step": 3 * N_PART * 16}
+
+    B.bh_destroy(h)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_PART, "theta": THETA, "eps": EPS, "dt": DT,
+                   "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                   "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
+                   "walk_shape": {"ppl": tuning[0], "warps_per_block": tuning[1]}},
+        "phase_ms_per_step": {"integrate": phase_ms[0] / nsteps, "build": build_ms, "walk": walk_ms},
+        "wall_ms_per_step": 1e3 * wall / args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fma_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fma_peak, "traffic": None,
+                     "kernel": "k_walk", "peak_source": "project FP32 FMA micro-benchmark",
+                     "interactions_per_launch": inter, "flops_per_interaction": FLOPS_PER_INTERACTION,
+                     "warp_iterations_per_launch": ws1["warp_iterations"],
+                     "lane_efficiency": ws1["interactions"] / (32.0 * ws1["warp_iterations"]),
+                     "slot_visits_per_launch": ws1["slot_visits"]},
+        "build_roofline": {"bound": "hbm", "achieved": build_gbs, "peak": peaks["hbm_gbs"],
+                           "unit": "GB/s", "frac": build_gbs / peaks["hbm_gbs"],
+                           "algorithmic_bytes": build_bytes, "nodes": n_nodes,
+                           "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"},
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        v, spent, threads = cpu_sample(pm, args.cpu_sample)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"one step: full FP64 tree build of {N_PART} particles "
+                                          f"(1 thread) + walk of {args.cpu_sample} random particles "
+                                          f"({threads} threads), extrapolated to N; {spent:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=1 << 20)
+    ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ppl", type=int, default=0, help="fix the walk shape (skip the autotuner)")
+    ap.add_argument("--warps", type=int, default=8)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -136,9 +136,12 @@ int bh_create(bh_system **out, const bh_params *p, int64_t n, const float *pos_m
 
 int bh_destroy(bh_system *s);
 
-/* Replaces positions/masses and velocities (n x 4 each; vel may be NULL to
- * keep the current velocities).  Invalidates the stored accelerations. */
-int bh_set_state(bh_system *s, const float *pos_mass, const float *vel, unsigned flags);
+/* Replaces the state (n x 4 each).  vel NULL keeps the current velocities.
+ * acc, if not NULL, is taken as the acceleration of the new positions (as
+ * returned by bh_get_state), so the next bh_step needs no extra force
+ * evaluation; if NULL the stored acceleration is invalidated. */
+int bh_set_state(bh_system *s, const float *pos_mass, const float *vel, const float *acc,
+                 unsigned flags);
 
 /* Builds the octree of the current positions (Section I; the tree-build
  * barrier of Section III): bounding cube and root centre of mass (FP64),
@@ -181,6 +184,14 @@ int bh_diagnostics(bh_system *s, double out[8]);
  * cells plus leaf particles it interacts with (its own leaf included).
  * counts: n uint32 in input order or NULL; *total receives the sum. */
 int bh_interaction_count(bh_system *s, uint32_t *counts, uint64_t *total);
+
+/* Work of one walk over the current tree (the counting walk above):
+ * interactions (accepted cells + leaf particles, summed over particles), warp
+ * iterations (nodes the warps visit: the union of their particles' walks) and
+ * particle-slot visits (nodes each particle itself visits, opened or taken).
+ * interactions / (32 x warp_iterations) is the walk's lane efficiency. */
+int bh_walk_stats(bh_system *s, uint64_t *interactions, uint64_t *warp_iterations,
+                  uint64_t *slot_visits);
 
 /* Walk launch shape: set explicitly, or pick by timing the candidates on the
  * current tree (cached per device, log2 N bucket and theta bucket).  Results

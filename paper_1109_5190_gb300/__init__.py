@@ -67,8 +67,8 @@ class System:
         binding.bh_get_state(self._h, pm, v, a)
         return pm, v, a
 
-    def set_state(self, pos_mass, vel=None):
-        binding.bh_set_state(self._h, pos_mass, vel)
+    def set_state(self, pos_mass, vel=None, acc=None):
+        binding.bh_set_state(self._h, pos_mass, vel, acc)
 
     def diagnostics(self):
         return binding.bh_diagnostics(self._h)

@@ -86,7 +86,7 @@ _SIGS = {
     "bh_params_default": ([P], I),
     "bh_create": ([P, P, I64, P, P, P, U], I),
     "bh_destroy": ([P], I),
-    "bh_set_state": ([P, P, P, U], I),
+    "bh_set_state": ([P, P, P, P, U], I),
     "bh_build_tree": ([P], I),
     "bh_get_tree": ([P, P, P, P, P, I64, P, P], I),
     "bh_compute_accel": ([P, P, U], I),
@@ -94,6 +94,7 @@ _SIGS = {
     "bh_get_state": ([P, P, P, P, U], I),
     "bh_diagnostics": ([P, P], I),
     "bh_interaction_count": ([P, P, P], I),
+    "bh_walk_stats": ([P, P, P, P], I),
     "bh_set_tuning": ([P, P], I),
     "bh_get_tuning": ([P, P], I),
     "bh_autotune": ([P, P], I),
@@ -187,10 +188,11 @@ def bh_destroy(h):
     return _check(lib.bh_destroy(h))
 
 
-def bh_set_state(h, pos_mass, vel=None):
+def bh_set_state(h, pos_mass, vel=None, acc=None):
     pp, f1 = _arr(pos_mass)
     vp, _ = _arr(vel)
-    return _check(lib.bh_set_state(h, pp, vp, f1))
+    ap, _ = _arr(acc)
+    return _check(lib.bh_set_state(h, pp, vp, ap, f1))
 
 
 def bh_build_tree(h):
@@ -211,6 +213,13 @@ def bh_get_tree(h, n: int, node_cap: int | None = None):
                            com.ctypes.data, M, C.byref(nn), cube.ctypes.data))
     M = nn.value
     return dict(keys=keys, order=order, nodes=nodes[:M], com_m=com[:M], cube=cube)
+
+
+def bh_node_count(h) -> int:
+    """Node count of the last built tree (bh_get_tree with no arrays)."""
+    nn = C.c_int64()
+    _check(lib.bh_get_tree(h, None, None, None, None, 0, C.byref(nn), None))
+    return nn.value
 
 
 def bh_compute_accel(h, acc_out=None):
@@ -243,6 +252,12 @@ def bh_interaction_count(h, n: int):
     tot = C.c_uint64()
     _check(lib.bh_interaction_count(h, counts.ctypes.data, C.byref(tot)))
     return counts, tot.value
+
+
+def bh_walk_stats(h) -> dict:
+    a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    _check(lib.bh_walk_stats(h, C.byref(a), C.byref(b), C.byref(c)))
+    return {"interactions": a.value, "warp_iterations": b.value, "slot_visits": c.value}
 
 
 def bh_set_tuning(h, ppl=2, warps_per_block=8, blocks_per_sm=0):

@@ -14,11 +14,19 @@
 //     virtual ids (double-buffered for the radix sort), the Morton-ordered
 //     copy spos of pos_mass, per-particle node counts / offsets.
 //   * Nodes of all trees in one array, each system's nodes contiguous, in
-//     depth-first pre-order (the canonical order): nodeA = (com_x, com_y,
-//     com_z, mass) and nodeB = (skip, crit2 bits, first, count), where skip
-//     is the index of the next node after the subtree and crit2 = s^2/theta^2
-//     (accept iff d^2 > crit2), -1 for a one-particle leaf (always taken as
-//     is) and -2 for a depth-cap bucket (particles one by one).
+//     depth-first pre-order (the canonical order):
+//       nodeA = (hx, hy, hz, mass)   FP32 centre of mass (high part), mass
+//       nodeB = (lx, ly, lz, crit2)  low part (com - h rounded to FP32) and
+//                                    the opening threshold s^2/theta^2
+//                                    (accept iff d^2 > crit2); -1 for a
+//                                    one-particle leaf (always taken as is),
+//                                    -2 for a depth-cap bucket (particles one
+//                                    by one)
+//       nodeC = (skip, first, count, level)  skip = index of the next node
+//                                    after the subtree
+//       nodeD = (mass, cx, cy, cz)   FP64, for the bottom-up pass and for
+//                                    re-deciding opening tests that fall
+//                                    within rounding distance of a tie
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -36,6 +44,9 @@ constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kRadixPasses = 8;  // 63-bit keys
 constexpr int kScanTile = 2048;
+// relative half-width of the band around an opening threshold inside which
+// the FP32 test is re-decided in FP64
+constexpr float kTieBand = 4e-6f;
 
 // device status codes (0 = ok)
 enum : int { ST_OK = 0, ST_CAPACITY = 1, ST_WALK_LIMIT = 2, ST_BAD_INPUT = 3 };
@@ -50,7 +61,7 @@ struct SysStatic {
     float eps2, G, inv_theta2, half_dt;
     float dt;
     int flags;
-    int pad[2];
+    double theta2;
 };
 
 struct SysDyn {
@@ -83,7 +94,8 @@ struct Small {
     unsigned M;
     unsigned needed;
     unsigned steps_done;
-    unsigned long long icount;
+    // counting walk: interactions, warp iterations, particle-slot node visits
+    unsigned long long wstats[3];
     unsigned queue;
     unsigned level_cnt[kNumLevels];
     unsigned level_cur[kNumLevels];
@@ -115,8 +127,9 @@ struct BuildBufs {
     uint32_t *ncount;     // n_total + 1
     uint32_t *noff;       // n_total + 1
     float4 *nodeA;
-    int4 *nodeB;
-    uint8_t *nlevel;
+    float4 *nodeB;
+    int4 *nodeC;
+    double4 *nodeD;
     uint32_t *nlist;
     unsigned node_cap;
     Small *small;
@@ -125,7 +138,6 @@ struct BuildBufs {
 };
 
 void launch_kick_drift_bbox(const BuildBufs &b, cudaStream_t st);
-void launch_bbox_final(const BuildBufs &b, cudaStream_t st);
 void launch_keys(const BuildBufs &b, cudaStream_t st);
 void launch_sort(const BuildBufs &b, cudaStream_t st);
 void launch_permute(const BuildBufs &b, cudaStream_t st);
@@ -144,7 +156,10 @@ void launch_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *partials,
 
 struct WalkArgs {
     const float4 *nodeA;
-    const int4 *nodeB;
+    const float4 *nodeB;
+    const int4 *nodeC;
+    const double4 *nodeD;
+    const SysDyn *dyn;
     const float4 *spos;
     const uint32_t *sid;  // sorted -> virtual id
     const uint32_t *noff;

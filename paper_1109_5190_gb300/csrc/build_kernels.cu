@@ -356,15 +356,16 @@ __device__ __forceinline__ int cell_end(const uint64_t *__restrict__ key, uint64
 __device__ __forceinline__ float pow2_neg(int l) { return __int_as_float((127 - l) << 23); }
 
 // Writes every node that starts at a particle: skip pointer (the first node
-// starting at the cell's end particle), opening threshold, first, count and
-// level, plus its slot in its level's list.  Root centres of mass come from
-// the FP64 reduction (or the particle itself for a one-particle system).
+// starting at the cell's end particle), first, count, level and opening
+// threshold, plus its slot in its level's list.  The root's centre of mass
+// comes from the FP64 reduction (or the particle itself for a one-particle
+// system); every other centre of mass is written by the bottom-up pass.
 __global__ void __launch_bounds__(kChunkThreads)
 k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
              const SysDyn *__restrict__ dyn, const uint64_t *__restrict__ key,
              const uint32_t *__restrict__ noff, const float4 *__restrict__ spos,
-             float4 *__restrict__ nodeA, int4 *__restrict__ nodeB,
-             uint8_t *__restrict__ nlevel, uint32_t *__restrict__ nlist, Small *__restrict__ sm)
+             float4 *__restrict__ nodeA, float4 *__restrict__ nodeB, int4 *__restrict__ nodeC,
+             double4 *__restrict__ nodeD, uint32_t *__restrict__ nlist, Small *__restrict__ sm)
 {
     if (halted(sm)) return;
     __shared__ unsigned h[kNumLevels], base[kNumLevels];
@@ -411,13 +412,21 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
                 const float sl = __fmul_rn(D.side, pow2_neg(l));
                 crit = __fmul_rn(__fmul_rn(sl, sl), S.inv_theta2);
             }
-            nodeB[n] = make_int4((int)noff[end], __float_as_int(crit), j, count);
-            nlevel[n] = (uint8_t)l;
+            nodeC[n] = make_int4((int)noff[end], j, count, l);
+            nodeB[n] = make_float4(0.f, 0.f, 0.f, crit);
             nlist[base[l] + atomicAdd(&h[l], 1u)] = n;
             if (l == 0) {
-                nodeA[n] = (count == 1) ? spos[j]
-                                        : make_float4(D.root_com[0], D.root_com[1],
-                                                      D.root_com[2], D.root_m);
+                if (count == 1) {
+                    const float4 p = spos[j];
+                    nodeA[n] = p;
+                    nodeD[n] = make_double4(p.w, p.x, p.y, p.z);
+                } else {
+                    const double cx = D.mx[0] / D.mtot, cy = D.mx[1] / D.mtot, cz = D.mx[2] / D.mtot;
+                    const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
+                    nodeA[n] = make_float4(hx, hy, hz, (float)D.mtot);
+                    nodeB[n] = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), crit);
+                    nodeD[n] = make_double4(D.mtot, cx, cy, cz);
+                }
             }
         }
     }
@@ -425,13 +434,15 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
 
 // ------------------------------------------------- centre of mass (A6)
 
-// Bottom-up, one launch per level (deepest first): a one-particle leaf takes
-// its particle; a bucket sums its particles; an internal node sums its
-// children (first child = next node, then skip pointers), each relative to
-// the first child's centre to keep FP32 cancellation small.
+// Bottom-up, one launch per level (deepest first), in FP64: a one-particle
+// leaf takes its particle; a bucket sums its particles; an internal node sums
+// its children (first child = next node, then skip pointers):
+// M = sum m_c, com = sum m_c com_c / M.  The FP64 result is kept (nodeD) and
+// split into an FP32 high part and the FP32-rounded remainder for the walk.
 __global__ void __launch_bounds__(256)
 k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
-            float4 *__restrict__ nodeA, const int4 *__restrict__ nodeB,
+            float4 *__restrict__ nodeA, float4 *__restrict__ nodeB,
+            const int4 *__restrict__ nodeC, double4 *__restrict__ nodeD,
             const Small *__restrict__ sm)
 {
     if (halted(sm)) return;
@@ -439,38 +450,38 @@ k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict_
     const unsigned off = sm->level_off[l];
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
         const unsigned n = nlist[off + k];
-        const int4 B = nodeB[n];
-        const float crit = __int_as_float(B.y);
+        const int4 C = nodeC[n];
+        const float crit = nodeB[n].w;
         if (crit == kLeafCrit) {
-            nodeA[n] = spos[B.z];
+            const float4 p = spos[C.y];
+            nodeA[n] = p;
+            nodeD[n] = make_double4(p.w, p.x, p.y, p.z);
             continue;
         }
-        float M = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-        float ox, oy, oz;
+        double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
         if (crit == kBucketCrit) {
-            const float4 o = spos[B.z];
-            ox = o.x; oy = o.y; oz = o.z;
-            for (int q = B.z; q < B.z + B.w; ++q) {
+            for (int q = C.y; q < C.y + C.z; ++q) {
                 const float4 p = spos[q];
-                M += p.w;
-                sx = fmaf(p.w, p.x - ox, sx);
-                sy = fmaf(p.w, p.y - oy, sy);
-                sz = fmaf(p.w, p.z - oz, sz);
+                const double m = p.w;
+                M += m;
+                sx += m * (double)p.x;
+                sy += m * (double)p.y;
+                sz += m * (double)p.z;
             }
         } else {
-            int ch = (int)n + 1;
-            const float4 o = nodeA[ch];
-            ox = o.x; oy = o.y; oz = o.z;
-            while (ch < B.x) {
-                const float4 p = nodeA[ch];
-                M += p.w;
-                sx = fmaf(p.w, p.x - ox, sx);
-                sy = fmaf(p.w, p.y - oy, sy);
-                sz = fmaf(p.w, p.z - oz, sz);
-                ch = nodeB[ch].x;
+            for (int ch = (int)n + 1; ch < C.x; ch = nodeC[ch].x) {
+                const double4 d = nodeD[ch];
+                M += d.x;
+                sx += d.x * d.y;
+                sy += d.x * d.z;
+                sz += d.x * d.w;
             }
         }
-        nodeA[n] = make_float4(ox + sx / M, oy + sy / M, oz + sz / M, M);
+        const double cx = sx / M, cy = sy / M, cz = sz / M;
+        const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
+        nodeD[n] = make_double4(M, cx, cy, cz);
+        nodeA[n] = make_float4(hx, hy, hz, (float)M);
+        nodeB[n] = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), crit);
     }
 }
 
@@ -601,38 +612,37 @@ __global__ void k_diag_final(const SysStatic *__restrict__ sys, const DiagPart *
 __global__ void __launch_bounds__(256)
 k_export(int sysid, const SysStatic *__restrict__ sys, const uint32_t *__restrict__ noff,
          const uint64_t *__restrict__ key, const uint32_t *__restrict__ sid,
-         const float4 *__restrict__ nodeA, const int4 *__restrict__ nodeB,
-         const uint8_t *__restrict__ nlevel, bh_node *__restrict__ out_nodes,
+         const float4 *__restrict__ nodeA, const float4 *__restrict__ nodeB,
+         const int4 *__restrict__ nodeC, bh_node *__restrict__ out_nodes,
          float4 *__restrict__ out_com, uint32_t *__restrict__ out_order)
 {
     const SysStatic S = sys[sysid];
     const unsigned n0 = noff[S.start], n1 = noff[S.start + S.n];
     const unsigned stride = gridDim.x * blockDim.x;
     for (unsigned n = n0 + blockIdx.x * blockDim.x + threadIdx.x; n < n1; n += stride) {
-        const int4 B = nodeB[n];
-        const int l = nlevel[n];
-        const uint64_t pre = (l == 0) ? 0ull : (key[B.z] >> (3 * (kLevels - l)));
+        const int4 C = nodeC[n];
+        const int l = C.w;
+        const uint64_t pre = (l == 0) ? 0ull : (key[C.y] >> (3 * (kLevels - l)));
         unsigned cm = 0;
-        const float crit = __int_as_float(B.y);
-        if (crit != kLeafCrit && crit != kBucketCrit) {
-            int ch = (int)n + 1;
-            while (ch < B.x) {
-                const int f = nodeB[ch].z;
-                cm |= 1u << (unsigned)((key[f] >> (3 * (kLevels - l - 1))) & 7u);
-                ch = nodeB[ch].x;
-            }
+        const float4 B = nodeB[n];
+        if (B.w != kLeafCrit && B.w != kBucketCrit) {
+            for (int ch = (int)n + 1; ch < C.x; ch = nodeC[ch].x)
+                cm |= 1u << (unsigned)((key[nodeC[ch].y] >> (3 * (kLevels - l - 1))) & 7u);
         }
         if (out_nodes) {
             bh_node o;
             o.prefix = pre;
-            o.first = (uint32_t)(B.z - S.start);
-            o.count = (uint32_t)B.w;
+            o.first = (uint32_t)(C.y - S.start);
+            o.count = (uint32_t)C.z;
             o.level = (uint8_t)l;
             o.childmask = (uint8_t)cm;
             for (int q = 0; q < 6; ++q) o.pad[q] = 0;
             out_nodes[n - n0] = o;
         }
-        if (out_com) out_com[n - n0] = nodeA[n];
+        if (out_com) {
+            const float4 A = nodeA[n];
+            out_com[n - n0] = make_float4(A.x + B.x, A.y + B.y, A.z + B.z, A.w);
+        }
     }
     if (out_order) {
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S.n; i += stride)
@@ -649,12 +659,6 @@ void launch_kick_drift_bbox(const BuildBufs &b, cudaStream_t st)
     k_kick_drift_box<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.mode, b.parts, b.small);
     k_box_final<<<b.nsys, 256, 0, st>>>(b.sys, b.dyn, b.parts, b.small);
     g_launches += 2;
-}
-
-void launch_bbox_final(const BuildBufs &b, cudaStream_t st)
-{
-    k_box_final<<<b.nsys, 256, 0, st>>>(b.sys, b.dyn, b.parts, b.small);
-    g_launches += 1;
 }
 
 void launch_keys(const BuildBufs &b, cudaStream_t st)
@@ -676,8 +680,8 @@ void launch_topology(const BuildBufs &b, cudaStream_t st)
     launch_scan(b.ncount, b.noff, b.n_total, b.scan_part, b.noff + b.n_total, &b.small->status, st);
     k_level_offsets<<<1, 32, 0, st>>>(b.small, b.noff, b.n_total, b.node_cap);
     k_topo_write<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.dyn, b.key0, b.noff,
-                                                      b.spos, b.nodeA, b.nodeB, b.nlevel,
-                                                      b.nlist, b.small);
+                                                      b.spos, b.nodeA, b.nodeB, b.nodeC,
+                                                      b.nodeD, b.nlist, b.small);
     g_launches += 2;
 }
 
@@ -685,7 +689,8 @@ void launch_com(const BuildBufs &b, cudaStream_t st)
 {
     const int grid = b.nsm * 8;
     for (int l = kLevels; l >= 1; --l) {
-        k_com_level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeA, b.nodeB, b.small);
+        k_com_level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeA, b.nodeB, b.nodeC, b.nodeD,
+                                          b.small);
         g_launches += 1;
     }
 }
@@ -719,7 +724,7 @@ void launch_export(const BuildBufs &b, int sysid, bh_node *nodes_dev, float4 *co
                    uint32_t *order_dev, cudaStream_t st)
 {
     k_export<<<b.nsm * 4, 256, 0, st>>>(sysid, b.sys, b.noff, b.key0, b.val0, b.nodeA, b.nodeB,
-                                        b.nlevel, nodes_dev, com_dev, order_dev);
+                                        b.nodeC, nodes_dev, com_dev, order_dev);
     g_launches += 1;
 }
 

@@ -183,7 +183,7 @@ struct Forest {
     bool tables_dirty = true;
 
     DevBuf d_sys, d_dyn, d_chunks, d_mode, d_parts, key0, key1, val0, val1, rs_counts, scan_part,
-        spos, ncount, noff, nodeA, nodeB, nlevel, nlist, d_small, d_diag_parts, d_diag_out,
+        spos, ncount, noff, nodeA, nodeB, nodeC, nodeD, nlist, d_small, d_diag_parts, d_diag_out,
         d_counts, d_export;
     unsigned node_cap = 0;
     struct TileSet {
@@ -272,8 +272,9 @@ struct Forest {
         b.ncount = ncount.as<uint32_t>();
         b.noff = noff.as<uint32_t>();
         b.nodeA = nodeA.as<float4>();
-        b.nodeB = nodeB.as<int4>();
-        b.nlevel = nlevel.as<uint8_t>();
+        b.nodeB = nodeB.as<float4>();
+        b.nodeC = nodeC.as<int4>();
+        b.nodeD = nodeD.as<double4>();
         b.nlist = nlist.as<uint32_t>();
         b.node_cap = node_cap;
         b.small = small();
@@ -286,8 +287,9 @@ struct Forest {
     {
         if (cap <= node_cap && nodeA.p) return BH_OK;
         TRY(nodeA.ensure(cap * sizeof(float4)));
-        TRY(nodeB.ensure(cap * sizeof(int4)));
-        TRY(nlevel.ensure(cap));
+        TRY(nodeB.ensure(cap * sizeof(float4)));
+        TRY(nodeC.ensure(cap * sizeof(int4)));
+        TRY(nodeD.ensure(cap * sizeof(double4)));
         TRY(nlist.ensure(cap * sizeof(uint32_t)));
         node_cap = (unsigned)cap;
         invalidate_graph();
@@ -324,6 +326,7 @@ struct Forest {
             d.half_dt = (float)(0.5 * S->dt);
             d.dt = (float)S->dt;
             d.flags = 0;
+            d.theta2 = S->theta * S->theta;
             start += S->n;
             if (start > (int64_t)INT_MAX / 2) return fail(BH_ERR_INVALID, "too many particles (limit 2^30)");
         }
@@ -424,7 +427,10 @@ struct Forest {
     {
         WalkArgs a;
         a.nodeA = nodeA.as<float4>();
-        a.nodeB = nodeB.as<int4>();
+        a.nodeB = nodeB.as<float4>();
+        a.nodeC = nodeC.as<int4>();
+        a.nodeD = nodeD.as<double4>();
+        a.dyn = d_dyn.as<SysDyn>();
         a.spos = spos.as<float4>();
         a.sid = val0.as<uint32_t>();
         a.noff = noff.as<uint32_t>();
@@ -500,7 +506,7 @@ struct Forest {
 
     int clear_status()
     {
-        CKR(cudaMemsetAsync(d_small.p, 0, offsetof(Small, icount), st));
+        CKR(cudaMemsetAsync(d_small.p, 0, offsetof(Small, wstats), st));
         return BH_OK;
     }
 
@@ -701,6 +707,7 @@ struct Forest {
         TRY(clear_status());
         reset_step_counters();
         WalkShape sh{1, 8, 0};
+        CKR(cudaMemsetAsync(small()->wstats, 0, sizeof(small()->wstats), st));
         launch_walk(walk_args(1, d_counts.as<uint32_t>()), sh, true, false, true, nsm, st);
         launches += 1;
         const SysStatic &S = h_sys[sys];
@@ -878,17 +885,20 @@ int bh_destroy(bh_system *s)
     return BH_OK;
 }
 
-int bh_set_state(bh_system *s, const float *pos_mass, const float *vel, unsigned flags)
+int bh_set_state(bh_system *s, const float *pos_mass, const float *vel, const float *acc,
+                 unsigned flags)
 {
     if (!s || !pos_mass) return fail(BH_ERR_INVALID, "null argument");
+    if (flags & ~BH_DEVICE_PTRS) return fail(BH_ERR_INVALID, "unknown flags");
     TRY(s->f.begin_call());
     SysState &S = *s->f.systems[0];
     if (!(flags & BH_DEVICE_PTRS) && !finite_state(S.n, pos_mass, vel))
         return fail(BH_ERR_INVALID, "non-finite coordinate or non-positive mass");
     TRY(upload4(S.pos(), pos_mass, S.n, flags, s->f.st));
     if (vel) TRY(upload4(S.vel(), vel, S.n, flags, s->f.st));
+    if (acc) TRY(upload4(S.acc(), acc, S.n, flags, s->f.st));
     if (flags & BH_DEVICE_PTRS) TRY(s->f.validate_device());
-    s->f.acc_valid = false;
+    s->f.acc_valid = acc != nullptr;
     s->f.tree_valid = false;
     return s->f.sync();
 }
@@ -957,6 +967,20 @@ int bh_interaction_count(bh_system *s, uint32_t *counts, uint64_t *total)
     if (!s) return fail(BH_ERR_INVALID, "null system");
     TRY(s->f.begin_call());
     return s->f.interaction_count(0, counts, total);
+}
+
+int bh_walk_stats(bh_system *s, uint64_t *interactions, uint64_t *warp_iterations,
+                  uint64_t *slot_visits)
+{
+    if (!s) return fail(BH_ERR_INVALID, "null system");
+    TRY(s->f.begin_call());
+    uint64_t tot = 0;
+    TRY(s->f.interaction_count(0, nullptr, &tot));
+    const Small &h = *s->f.h_small;
+    if (interactions) *interactions = h.wstats[0];
+    if (warp_iterations) *warp_iterations = h.wstats[1];
+    if (slot_visits) *slot_visits = h.wstats[2];
+    return BH_OK;
 }
 
 int bh_set_tuning(bh_system *s, const bh_tuning *t)

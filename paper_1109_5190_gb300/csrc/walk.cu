@@ -53,6 +53,22 @@ __device__ __forceinline__ void acc_add(float &s, float &c, float x)
     }
 }
 
+// The paper's opening test in FP64, for a test whose FP32 value lies within
+// rounding distance of the threshold: s^2 < theta^2 d^2 with s = side 2^-level
+// and d from the FP64 centre of mass (the same formula and operation order as
+// the FP64 definition, so both decide alike).
+__device__ __noinline__ bool accept_fp64(const double4 *__restrict__ nodeD, int node, int level,
+                                         float px, float py, float pz, double side, double theta2)
+{
+    const double4 D = nodeD[node];
+    const double dx = __dsub_rn(D.y, (double)px);
+    const double dy = __dsub_rn(D.z, (double)py);
+    const double dz = __dsub_rn(D.w, (double)pz);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    const double s = side * __longlong_as_double((long long)(1023 - level) << 52);
+    return __dmul_rn(s, s) < __dmul_rn(theta2, d2);
+}
+
 template <int PPL, bool KAHAN, bool POT, bool COUNT>
 __global__ void k_walk(WalkArgs a)
 {
@@ -70,17 +86,20 @@ __global__ void k_walk(WalkArgs a)
         const int root = (int)a.noff[sstart];
         const int nend = (int)a.noff[sstart + S.n];
         const float eps2 = S.eps2;
+        const double theta2 = S.theta2;
+        const double side = (double)a.dyn[tl.sys].side;
 
         float px[PPL], py[PPL], pz[PPL];
         int nxt[PPL], myj[PPL];
         float ax[PPL], ay[PPL], az[PPL], cx[PPL], cy[PPL], cz[PPL], pp[PPL], cp[PPL];
-        unsigned cnt[PPL];
+        unsigned cnt[PPL], vis[PPL];
+        unsigned iters = 0;
 #pragma unroll
         for (int k = 0; k < PPL; ++k) {
             const int o = k * 32 + lane;
             myj[k] = tl.start + o;
             ax[k] = ay[k] = az[k] = cx[k] = cy[k] = cz[k] = pp[k] = cp[k] = 0.f;
-            cnt[k] = 0;
+            cnt[k] = vis[k] = 0;
             if (o < tl.count) {
                 const float4 P = a.spos[myj[k]];
                 px[k] = P.x; py[k] = P.y; pz[k] = P.z;
@@ -97,15 +116,21 @@ __global__ void k_walk(WalkArgs a)
             for (int k = 1; k < PPL; ++k) m = min(m, nxt[k]);
             const int cur = (int)__reduce_min_sync(FULL, (unsigned)m);
             if (cur >= nend) break;
+            if (COUNT) {
+                ++iters;
+#pragma unroll
+                for (int k = 0; k < PPL; ++k) vis[k] += nxt[k] == cur;
+            }
             const float4 A = __ldg(&a.nodeA[cur]);
-            const int4 B = __ldg(&a.nodeB[cur]);
-            if (B.x <= cur) {  // corrupt skip pointer: report, never spin
+            const float4 Bf = __ldg(&a.nodeB[cur]);
+            const int4 C = __ldg(&a.nodeC[cur]);
+            if (C.x <= cur) {  // corrupt skip pointer: report, never spin
                 if (lane == 0) atomicExch(&sm->status, ST_WALK_LIMIT);
                 break;
             }
-            const float crit = __int_as_float(B.y);
+            const float crit = Bf.w;
             if (crit == kBucketCrit) {
-                for (int q = B.z; q < B.z + B.w; ++q) {
+                for (int q = C.y; q < C.y + C.z; ++q) {
                     const float4 P = __ldg(&a.spos[q]);
 #pragma unroll
                     for (int k = 0; k < PPL; ++k) {
@@ -125,14 +150,22 @@ __global__ void k_walk(WalkArgs a)
                 }
 #pragma unroll
                 for (int k = 0; k < PPL; ++k)
-                    if (nxt[k] == cur) nxt[k] = B.x;
+                    if (nxt[k] == cur) nxt[k] = C.x;
             } else {
+                const float band = crit * kTieBand;  // negative for leaves: never a tie
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
                     if (nxt[k] == cur) {
-                        const float dx = A.x - px[k], dy = A.y - py[k], dz = A.z - pz[k];
+                        // distance to the centre of mass from its high and low FP32 parts
+                        const float dx = (A.x - px[k]) + Bf.x;
+                        const float dy = (A.y - py[k]) + Bf.y;
+                        const float dz = (A.z - pz[k]) + Bf.z;
                         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        if (d2 > crit) {
+                        const float diff = d2 - crit;
+                        bool acc = diff > 0.f;
+                        if (fabsf(diff) < band)
+                            acc = accept_fp64(a.nodeD, cur, C.w, px[k], py[k], pz[k], side, theta2);
+                        if (acc) {
                             const float r2 = d2 + eps2;
                             const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
                             const float mi = A.w * inv;
@@ -140,10 +173,10 @@ __global__ void k_walk(WalkArgs a)
                             acc_add<KAHAN>(ax[k], cx[k], mi3 * dx);
                             acc_add<KAHAN>(ay[k], cy[k], mi3 * dy);
                             acc_add<KAHAN>(az[k], cz[k], mi3 * dz);
-                            if (POT && !(crit == kLeafCrit && B.z == myj[k]))
+                            if (POT && !(crit == kLeafCrit && C.y == myj[k]))
                                 acc_add<KAHAN>(pp[k], cp[k], mi);
                             if (COUNT) cnt[k] += 1;
-                            nxt[k] = B.x;
+                            nxt[k] = C.x;
                         } else {
                             nxt[k] = cur + 1;
                         }
@@ -152,6 +185,23 @@ __global__ void k_walk(WalkArgs a)
             }
         }
 
+        if (COUNT) {
+            unsigned long long ci = 0, cv = 0;
+#pragma unroll
+            for (int k = 0; k < PPL; ++k) {
+                ci += (k * 32 + lane < tl.count) ? cnt[k] : 0u;
+                cv += (k * 32 + lane < tl.count) ? vis[k] : 0u;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                ci += __shfl_down_sync(FULL, ci, o);
+                cv += __shfl_down_sync(FULL, cv, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&sm->wstats[0], ci);
+                atomicAdd(&sm->wstats[1], (unsigned long long)iters);
+                atomicAdd(&sm->wstats[2], cv);
+            }
+        }
         const float G = S.G;
         float4 *acc = S.acc;
 #pragma unroll

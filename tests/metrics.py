@@ -17,10 +17,21 @@ def accel_errors(a_gpu, a_ref):
     a_ref = np.asarray(a_ref, dtype=np.float64)[:, :3]
     d = np.linalg.norm(a_gpu - a_ref, axis=1)
     r = np.linalg.norm(a_ref, axis=1)
-    rms = np.sqrt(np.mean(r * r)) if r.size else 0.0
-    rel = d / np.where(r > 0, r, np.inf)
-    relmax = d / np.maximum(r, 1e-3 * rms)
-    return float(np.percentile(rel, 99)) if rel.size else 0.0, float(relmax.max()) if rel.size else 0.0
+    if r.size == 0:
+        return 0.0, 0.0
+    rms = np.sqrt(np.mean(r * r))
+
+    def ratio(num, den):
+        # 0/0 (an exactly zero force reproduced exactly) is no error
+        out = np.zeros_like(num)
+        nz = num > 0
+        with np.errstate(divide="ignore"):
+            out[nz] = num[nz] / den[nz]
+        return out
+
+    rel = ratio(d, r)
+    relmax = ratio(d, np.maximum(r, 1e-3 * rms))
+    return float(np.percentile(rel, 99)), float(relmax.max())
 
 
 def assert_accel_close(a_gpu, a_ref, p99=P99_TOL, mx=MAX_TOL, what=""):

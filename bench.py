@@ -181,7 +181,7 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     if args.ppl:
-        B.bh_set_tuning(h, args.ppl, args.warps, 0)
+        B.bh_set_tuning(h, args.ppl, args.warps, 0, args.group)
         tuning = B.bh_get_tuning(h)
     else:
         tuning = B.bh_autotune(h)
@@ -255,7 +255,8 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "n": N_PART, "theta": THETA, "eps": EPS, "dt": DT,
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
-                   "walk_shape": {"ppl": tuning[0], "warps_per_block": tuning[1]}},
+                   "walk_shape": {"ppl": tuning[0], "warps_per_block": tuning[1],
+                                  "group": tuning[3]}},
         "phase_ms_per_step": {"integrate": phase_ms[0] / nsteps, "build": build_ms, "walk": walk_ms},
         "wall_ms_per_step": 1e3 * wall / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fma_peak, "unit": "TFLOP/s",
@@ -298,6 +299,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ppl", type=int, default=0, help="fix the walk shape (skip the autotuner)")
     ap.add_argument("--warps", type=int, default=8)
+    ap.add_argument("--group", type=int, default=1, help="lanes voting together (1 or 32)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

@@ -98,15 +98,20 @@ typedef struct bh_node {
 } bh_node;
 
 /* Walk launch shape (the autotuner's search space).
- *   ppl             particles per lane (1, 2 or 4): a warp task is a tile of
- *                   32*ppl consecutive Morton-sorted particles
- *   warps_per_block 2..16
- *   blocks_per_sm   0 = as many as fit */
+ *   ppl             particles per lane (1, 2 or 4; 1 or 2 when group is 1): a
+ *                   warp task is a tile of 32*ppl consecutive Morton-sorted
+ *                   particles
+ *   warps_per_block 1..32
+ *   blocks_per_sm   0 = as many as fit
+ *   group           lanes that vote together on the next node: 32 = the warp
+ *                   walks the union of its particles' traversals (one
+ *                   broadcast node load per step), 1 = every lane walks its
+ *                   own particles' traversal */
 typedef struct bh_tuning {
     int ppl;
     int warps_per_block;
     int blocks_per_sm;
-    int reserved;
+    int group;
 } bh_tuning;
 
 typedef struct bh_system bh_system;

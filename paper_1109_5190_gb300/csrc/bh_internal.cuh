@@ -14,17 +14,19 @@
 //     virtual ids (double-buffered for the radix sort), the Morton-ordered
 //     copy spos of pos_mass, per-particle node counts / offsets.
 //   * Nodes of all trees in one array, each system's nodes contiguous, in
-//     depth-first pre-order (the canonical order):
-//       nodeA = (hx, hy, hz, mass)   FP32 centre of mass (high part), mass
-//       nodeB = (lx, ly, lz, crit2)  low part (com - h rounded to FP32) and
+//     depth-first pre-order (the canonical order).  The walk's record WNode
+//     (48 bytes, one array so a lane's three loads share two sectors) is
+//       a = (hx, hy, hz, mass)   FP32 centre of mass (high part), mass
+//       b = (lx, ly, lz, crit2)  low part (com - h rounded to FP32) and
 //                                    the opening threshold s^2/theta^2
 //                                    (accept iff d^2 > crit2); -1 for a
 //                                    one-particle leaf (always taken as is),
 //                                    -2 for a depth-cap bucket (particles one
 //                                    by one)
-//       nodeC = (skip, first, count, level)  skip = index of the next node
+//       c = (skip, first, count, level)  skip = index of the next node
 //                                    after the subtree
-//       nodeD = (mass, cx, cy, cz)   FP64, for the bottom-up pass and for
+//     and a separate FP64 array nodeD = (mass, cx, cy, cz), for the
+//     bottom-up pass and for
 //                                    re-deciding opening tests that fall
 //                                    within rounding distance of a tie
 #pragma once
@@ -102,6 +104,12 @@ struct Small {
     unsigned level_off[kNumLevels + 1];
 };
 
+struct __align__(16) WNode {
+    float4 a;
+    float4 b;
+    int4 c;
+};
+
 struct Tile {
     int start;  // virtual index of the first particle (sorted order)
     int count;  // <= 32 * ppl
@@ -126,9 +134,7 @@ struct BuildBufs {
     float4 *spos;
     uint32_t *ncount;     // n_total + 1
     uint32_t *noff;       // n_total + 1
-    float4 *nodeA;
-    float4 *nodeB;
-    int4 *nodeC;
+    WNode *nodeW;
     double4 *nodeD;
     uint32_t *nlist;
     unsigned node_cap;
@@ -155,9 +161,7 @@ void launch_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *partials,
                  uint32_t *total, const int *status, cudaStream_t st);
 
 struct WalkArgs {
-    const float4 *nodeA;
-    const float4 *nodeB;
-    const int4 *nodeC;
+    const WNode *nodeW;
     const double4 *nodeD;
     const SysDyn *dyn;
     const float4 *spos;
@@ -171,10 +175,14 @@ struct WalkArgs {
     uint32_t *counts;  // per-particle interaction counts (virtual order) or null
 };
 
+// ppl: particles per lane; group: lanes that vote together on the next node
+// (32 = the whole warp walks the union of its particles' traversals, 1 =
+// every lane walks its own particles' traversal independently)
 struct WalkShape {
     int ppl;
     int warps;
     int blocks_per_sm;
+    int group;
 };
 
 // kahan / potential / counting variants; returns number of kernel launches

@@ -364,8 +364,8 @@ __global__ void __launch_bounds__(kChunkThreads)
 k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
              const SysDyn *__restrict__ dyn, const uint64_t *__restrict__ key,
              const uint32_t *__restrict__ noff, const float4 *__restrict__ spos,
-             float4 *__restrict__ nodeA, float4 *__restrict__ nodeB, int4 *__restrict__ nodeC,
-             double4 *__restrict__ nodeD, uint32_t *__restrict__ nlist, Small *__restrict__ sm)
+             WNode *__restrict__ nodeW, double4 *__restrict__ nodeD,
+             uint32_t *__restrict__ nlist, Small *__restrict__ sm)
 {
     if (halted(sm)) return;
     __shared__ unsigned h[kNumLevels], base[kNumLevels];
@@ -412,19 +412,19 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
                 const float sl = __fmul_rn(D.side, pow2_neg(l));
                 crit = __fmul_rn(__fmul_rn(sl, sl), S.inv_theta2);
             }
-            nodeC[n] = make_int4((int)noff[end], j, count, l);
-            nodeB[n] = make_float4(0.f, 0.f, 0.f, crit);
+            nodeW[n].c = make_int4((int)noff[end], j, count, l);
+            nodeW[n].b = make_float4(0.f, 0.f, 0.f, crit);
             nlist[base[l] + atomicAdd(&h[l], 1u)] = n;
             if (l == 0) {
                 if (count == 1) {
                     const float4 p = spos[j];
-                    nodeA[n] = p;
+                    nodeW[n].a = p;
                     nodeD[n] = make_double4(p.w, p.x, p.y, p.z);
                 } else {
                     const double cx = D.mx[0] / D.mtot, cy = D.mx[1] / D.mtot, cz = D.mx[2] / D.mtot;
                     const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
-                    nodeA[n] = make_float4(hx, hy, hz, (float)D.mtot);
-                    nodeB[n] = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), crit);
+                    nodeW[n].a = make_float4(hx, hy, hz, (float)D.mtot);
+                    nodeW[n].b = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), crit);
                     nodeD[n] = make_double4(D.mtot, cx, cy, cz);
                 }
             }
@@ -441,20 +441,18 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
 // split into an FP32 high part and the FP32-rounded remainder for the walk.
 __global__ void __launch_bounds__(256)
 k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
-            float4 *__restrict__ nodeA, float4 *__restrict__ nodeB,
-            const int4 *__restrict__ nodeC, double4 *__restrict__ nodeD,
-            const Small *__restrict__ sm)
+            WNode *__restrict__ nodeW, double4 *__restrict__ nodeD, const Small *__restrict__ sm)
 {
     if (halted(sm)) return;
     const unsigned cnt = sm->level_cnt[l];
     const unsigned off = sm->level_off[l];
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
         const unsigned n = nlist[off + k];
-        const int4 C = nodeC[n];
-        const float crit = nodeB[n].w;
+        const int4 C = nodeW[n].c;
+        const float crit = nodeW[n].b.w;
         if (crit == kLeafCrit) {
             const float4 p = spos[C.y];
-            nodeA[n] = p;
+            nodeW[n].a = p;
             nodeD[n] = make_double4(p.w, p.x, p.y, p.z);
             continue;
         }
@@ -469,7 +467,7 @@ k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict_
                 sz += m * (double)p.z;
             }
         } else {
-            for (int ch = (int)n + 1; ch < C.x; ch = nodeC[ch].x) {
+            for (int ch = (int)n + 1; ch < C.x; ch = nodeW[ch].c.x) {
                 const double4 d = nodeD[ch];
                 M += d.x;
                 sx += d.x * d.y;
@@ -480,8 +478,8 @@ k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict_
         const double cx = sx / M, cy = sy / M, cz = sz / M;
         const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
         nodeD[n] = make_double4(M, cx, cy, cz);
-        nodeA[n] = make_float4(hx, hy, hz, (float)M);
-        nodeB[n] = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), crit);
+        nodeW[n].a = make_float4(hx, hy, hz, (float)M);
+        nodeW[n].b = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), crit);
     }
 }
 
@@ -612,22 +610,21 @@ __global__ void k_diag_final(const SysStatic *__restrict__ sys, const DiagPart *
 __global__ void __launch_bounds__(256)
 k_export(int sysid, const SysStatic *__restrict__ sys, const uint32_t *__restrict__ noff,
          const uint64_t *__restrict__ key, const uint32_t *__restrict__ sid,
-         const float4 *__restrict__ nodeA, const float4 *__restrict__ nodeB,
-         const int4 *__restrict__ nodeC, bh_node *__restrict__ out_nodes,
+         const WNode *__restrict__ nodeW, bh_node *__restrict__ out_nodes,
          float4 *__restrict__ out_com, uint32_t *__restrict__ out_order)
 {
     const SysStatic S = sys[sysid];
     const unsigned n0 = noff[S.start], n1 = noff[S.start + S.n];
     const unsigned stride = gridDim.x * blockDim.x;
     for (unsigned n = n0 + blockIdx.x * blockDim.x + threadIdx.x; n < n1; n += stride) {
-        const int4 C = nodeC[n];
+        const int4 C = nodeW[n].c;
         const int l = C.w;
         const uint64_t pre = (l == 0) ? 0ull : (key[C.y] >> (3 * (kLevels - l)));
         unsigned cm = 0;
-        const float4 B = nodeB[n];
+        const float4 B = nodeW[n].b;
         if (B.w != kLeafCrit && B.w != kBucketCrit) {
-            for (int ch = (int)n + 1; ch < C.x; ch = nodeC[ch].x)
-                cm |= 1u << (unsigned)((key[nodeC[ch].y] >> (3 * (kLevels - l - 1))) & 7u);
+            for (int ch = (int)n + 1; ch < C.x; ch = nodeW[ch].c.x)
+                cm |= 1u << (unsigned)((key[nodeW[ch].c.y] >> (3 * (kLevels - l - 1))) & 7u);
         }
         if (out_nodes) {
             bh_node o;
@@ -640,7 +637,7 @@ k_export(int sysid, const SysStatic *__restrict__ sys, const uint32_t *__restric
             out_nodes[n - n0] = o;
         }
         if (out_com) {
-            const float4 A = nodeA[n];
+            const float4 A = nodeW[n].a;
             out_com[n - n0] = make_float4(A.x + B.x, A.y + B.y, A.z + B.z, A.w);
         }
     }
@@ -680,8 +677,7 @@ void launch_topology(const BuildBufs &b, cudaStream_t st)
     launch_scan(b.ncount, b.noff, b.n_total, b.scan_part, b.noff + b.n_total, &b.small->status, st);
     k_level_offsets<<<1, 32, 0, st>>>(b.small, b.noff, b.n_total, b.node_cap);
     k_topo_write<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.dyn, b.key0, b.noff,
-                                                      b.spos, b.nodeA, b.nodeB, b.nodeC,
-                                                      b.nodeD, b.nlist, b.small);
+                                                      b.spos, b.nodeW, b.nodeD, b.nlist, b.small);
     g_launches += 2;
 }
 
@@ -689,8 +685,7 @@ void launch_com(const BuildBufs &b, cudaStream_t st)
 {
     const int grid = b.nsm * 8;
     for (int l = kLevels; l >= 1; --l) {
-        k_com_level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeA, b.nodeB, b.nodeC, b.nodeD,
-                                          b.small);
+        k_com_level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeW, b.nodeD, b.small);
         g_launches += 1;
     }
 }
@@ -723,8 +718,8 @@ void launch_diagnostics(const BuildBufs &b, DiagPart *parts, double *out, cudaSt
 void launch_export(const BuildBufs &b, int sysid, bh_node *nodes_dev, float4 *com_dev,
                    uint32_t *order_dev, cudaStream_t st)
 {
-    k_export<<<b.nsm * 4, 256, 0, st>>>(sysid, b.sys, b.noff, b.key0, b.val0, b.nodeA, b.nodeB,
-                                        b.nodeC, nodes_dev, com_dev, order_dev);
+    k_export<<<b.nsm * 4, 256, 0, st>>>(sysid, b.sys, b.noff, b.key0, b.val0, b.nodeW,
+                                        nodes_dev, com_dev, order_dev);
     g_launches += 1;
 }
 

@@ -183,7 +183,7 @@ struct Forest {
     bool tables_dirty = true;
 
     DevBuf d_sys, d_dyn, d_chunks, d_mode, d_parts, key0, key1, val0, val1, rs_counts, scan_part,
-        spos, ncount, noff, nodeA, nodeB, nodeC, nodeD, nlist, d_small, d_diag_parts, d_diag_out,
+        spos, ncount, noff, nodeW, nodeD, nlist, d_small, d_diag_parts, d_diag_out,
         d_counts, d_export;
     unsigned node_cap = 0;
     struct TileSet {
@@ -195,7 +195,7 @@ struct Forest {
 
     bool acc_valid = false;
     bool tree_valid = false;
-    bh_tuning tune{2, 8, 0, 0};
+    bh_tuning tune{1, 8, 0, 1};
 
     cudaGraphExec_t gexec = nullptr;
     int g_nsteps = -1;
@@ -271,9 +271,7 @@ struct Forest {
         b.spos = spos.as<float4>();
         b.ncount = ncount.as<uint32_t>();
         b.noff = noff.as<uint32_t>();
-        b.nodeA = nodeA.as<float4>();
-        b.nodeB = nodeB.as<float4>();
-        b.nodeC = nodeC.as<int4>();
+        b.nodeW = nodeW.as<WNode>();
         b.nodeD = nodeD.as<double4>();
         b.nlist = nlist.as<uint32_t>();
         b.node_cap = node_cap;
@@ -285,10 +283,8 @@ struct Forest {
 
     int ensure_nodes(size_t cap)
     {
-        if (cap <= node_cap && nodeA.p) return BH_OK;
-        TRY(nodeA.ensure(cap * sizeof(float4)));
-        TRY(nodeB.ensure(cap * sizeof(float4)));
-        TRY(nodeC.ensure(cap * sizeof(int4)));
+        if (cap <= node_cap && nodeW.p) return BH_OK;
+        TRY(nodeW.ensure(cap * sizeof(WNode)));
         TRY(nodeD.ensure(cap * sizeof(double4)));
         TRY(nlist.ensure(cap * sizeof(uint32_t)));
         node_cap = (unsigned)cap;
@@ -426,9 +422,7 @@ struct Forest {
     WalkArgs walk_args(int ppl, uint32_t *counts) const
     {
         WalkArgs a;
-        a.nodeA = nodeA.as<float4>();
-        a.nodeB = nodeB.as<float4>();
-        a.nodeC = nodeC.as<int4>();
+        a.nodeW = nodeW.as<WNode>();
         a.nodeD = nodeD.as<double4>();
         a.dyn = d_dyn.as<SysDyn>();
         a.spos = spos.as<float4>();
@@ -444,7 +438,10 @@ struct Forest {
         return a;
     }
 
-    WalkShape shape() const { return WalkShape{tune.ppl, tune.warps_per_block, tune.blocks_per_sm}; }
+    WalkShape shape() const
+    {
+        return WalkShape{tune.ppl, tune.warps_per_block, tune.blocks_per_sm, tune.group};
+    }
     bool kahan() const { return !(flags & BH_NO_KAHAN); }
     bool pot() const { return (flags & BH_POTENTIAL) != 0; }
 
@@ -632,18 +629,20 @@ struct Forest {
             }
         }
         TRY(ensure_tree());
-        const int ppls[3] = {1, 2, 4};
+        // (group, particles per lane) candidates x warps per block
+        const int shapes[5][2] = {{1, 1}, {1, 2}, {32, 1}, {32, 2}, {32, 4}};
         const int warps[3] = {4, 8, 16};
         cudaEvent_t e0, e1;
         CKR(cudaEventCreate(&e0));
         CKR(cudaEventCreate(&e1));
         float best_ms = 1e30f;
         bh_tuning pick = tune;
-        for (int p : ppls) {
+        for (const auto &gp : shapes) {
+            const int g = gp[0], p = gp[1];
             TRY(ensure_tiles(p));
             for (int w : warps) {
-                bh_tuning t{p, w, 0, 0};
-                WalkShape sh{p, w, 0};
+                bh_tuning t{p, w, 0, g};
+                WalkShape sh{p, w, 0, g};
                 if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0) continue;
                 float ms_best = 1e30f;
                 for (int rep = 0; rep < 3; ++rep) {
@@ -677,13 +676,14 @@ struct Forest {
     int set_tuning(const bh_tuning *t)
     {
         if (!t || (t->ppl != 1 && t->ppl != 2 && t->ppl != 4) || t->warps_per_block < 1 ||
-            t->warps_per_block > 32 || t->blocks_per_sm < 0)
-            return fail(BH_ERR_INVALID, "bad tuning (ppl 1/2/4, warps 1..32, blocks_per_sm >= 0)");
-        WalkShape sh{t->ppl, t->warps_per_block, t->blocks_per_sm};
+            t->warps_per_block > 32 || t->blocks_per_sm < 0 || (t->group != 1 && t->group != 32) ||
+            (t->group == 1 && t->ppl == 4))
+            return fail(BH_ERR_INVALID, "bad tuning (group 1 with ppl 1/2 or group 32 with ppl "
+                                        "1/2/4; warps 1..32; blocks_per_sm >= 0)");
+        WalkShape sh{t->ppl, t->warps_per_block, t->blocks_per_sm, t->group};
         if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0)
             return fail(BH_ERR_INVALID, "walk shape does not fit on an SM");
         tune = *t;
-        tune.reserved = 0;
         return BH_OK;
     }
 
@@ -706,7 +706,7 @@ struct Forest {
         TRY(ensure_tiles(1));
         TRY(clear_status());
         reset_step_counters();
-        WalkShape sh{1, 8, 0};
+        WalkShape sh{1, 8, 0, tune.group};
         CKR(cudaMemsetAsync(small()->wstats, 0, sizeof(small()->wstats), st));
         launch_walk(walk_args(1, d_counts.as<uint32_t>()), sh, true, false, true, nsm, st);
         launches += 1;

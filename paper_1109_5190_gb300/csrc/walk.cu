@@ -69,9 +69,33 @@ __device__ __noinline__ bool accept_fp64(const double4 *__restrict__ nodeD, int 
     return __dmul_rn(s, s) < __dmul_rn(theta2, d2);
 }
 
-template <int PPL, bool KAHAN, bool POT, bool COUNT>
+// One softened monopole term added to a particle slot's sums.
+template <bool KAHAN, bool POT, bool COUNT>
+__device__ __forceinline__ void interact(float m, float dx, float dy, float dz, float d2, float eps2,
+                                         bool self, float &ax, float &ay, float &az, float &cx,
+                                         float &cy, float &cz, float &pp, float &cp, unsigned &cnt)
+{
+    const float r2 = d2 + eps2;
+    const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float mi = m * inv;
+    const float mi3 = mi * inv * inv;
+    acc_add<KAHAN>(ax, cx, mi3 * dx);
+    acc_add<KAHAN>(ay, cy, mi3 * dy);
+    acc_add<KAHAN>(az, cz, mi3 * dz);
+    if (POT && !self) acc_add<KAHAN>(pp, cp, mi);
+    if (COUNT) cnt += 1;
+}
+
+// GROUP = 32: the warp votes (__reduce_min_sync) on the next node and visits
+// the union of its particles' traversals, one broadcast node load per step.
+// GROUP = 1: no vote; every lane advances through its own particles'
+// traversal (loads diverge, no lane waits on nodes it does not need).
+// Either way each particle visits exactly its own nodes in increasing index
+// order, so its sums -- and the results -- do not depend on the shape.
+template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT>
 __global__ void k_walk(WalkArgs a)
 {
+    static_assert(GROUP == 1 || GROUP == 32, "vote group is a lane or the warp");
     const int lane = threadIdx.x & 31;
     Small *sm = a.small;
     if (sm->status) return;
@@ -111,21 +135,22 @@ __global__ void k_walk(WalkArgs a)
         }
 
         for (;;) {
-            int m = nxt[0];
+            int cur = nxt[0];
 #pragma unroll
-            for (int k = 1; k < PPL; ++k) m = min(m, nxt[k]);
-            const int cur = (int)__reduce_min_sync(FULL, (unsigned)m);
+            for (int k = 1; k < PPL; ++k) cur = min(cur, nxt[k]);
+            if (GROUP == 32) cur = (int)__reduce_min_sync(FULL, (unsigned)cur);
             if (cur >= nend) break;
             if (COUNT) {
                 ++iters;
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) vis[k] += nxt[k] == cur;
             }
-            const float4 A = __ldg(&a.nodeA[cur]);
-            const float4 Bf = __ldg(&a.nodeB[cur]);
-            const int4 C = __ldg(&a.nodeC[cur]);
+            const WNode *np = a.nodeW + cur;
+            const float4 A = __ldg(&np->a);
+            const float4 Bf = __ldg(&np->b);
+            const int4 C = __ldg(&np->c);
             if (C.x <= cur) {  // corrupt skip pointer: report, never spin
-                if (lane == 0) atomicExch(&sm->status, ST_WALK_LIMIT);
+                atomicExch(&sm->status, ST_WALK_LIMIT);
                 break;
             }
             const float crit = Bf.w;
@@ -136,15 +161,10 @@ __global__ void k_walk(WalkArgs a)
                     for (int k = 0; k < PPL; ++k) {
                         if (nxt[k] == cur) {
                             const float dx = P.x - px[k], dy = P.y - py[k], dz = P.z - pz[k];
-                            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-                            const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                            const float mi = P.w * inv;
-                            const float mi3 = mi * inv * inv;
-                            acc_add<KAHAN>(ax[k], cx[k], mi3 * dx);
-                            acc_add<KAHAN>(ay[k], cy[k], mi3 * dy);
-                            acc_add<KAHAN>(az[k], cz[k], mi3 * dz);
-                            if (POT && q != myj[k]) acc_add<KAHAN>(pp[k], cp[k], mi);
-                            if (COUNT) cnt[k] += 1;
+                            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                            interact<KAHAN, POT, COUNT>(P.w, dx, dy, dz, d2, eps2, q == myj[k],
+                                                        ax[k], ay[k], az[k], cx[k], cy[k], cz[k],
+                                                        pp[k], cp[k], cnt[k]);
                         }
                     }
                 }
@@ -166,16 +186,10 @@ __global__ void k_walk(WalkArgs a)
                         if (fabsf(diff) < band)
                             acc = accept_fp64(a.nodeD, cur, C.w, px[k], py[k], pz[k], side, theta2);
                         if (acc) {
-                            const float r2 = d2 + eps2;
-                            const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                            const float mi = A.w * inv;
-                            const float mi3 = mi * inv * inv;
-                            acc_add<KAHAN>(ax[k], cx[k], mi3 * dx);
-                            acc_add<KAHAN>(ay[k], cy[k], mi3 * dy);
-                            acc_add<KAHAN>(az[k], cz[k], mi3 * dz);
-                            if (POT && !(crit == kLeafCrit && C.y == myj[k]))
-                                acc_add<KAHAN>(pp[k], cp[k], mi);
-                            if (COUNT) cnt[k] += 1;
+                            interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2,
+                                                        crit == kLeafCrit && C.y == myj[k],
+                                                        ax[k], ay[k], az[k], cx[k], cy[k], cz[k],
+                                                        pp[k], cp[k], cnt[k]);
                             nxt[k] = C.x;
                         } else {
                             nxt[k] = cur + 1;
@@ -186,7 +200,7 @@ __global__ void k_walk(WalkArgs a)
         }
 
         if (COUNT) {
-            unsigned long long ci = 0, cv = 0;
+            unsigned long long ci = 0, cv = 0, it = iters;
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
                 ci += (k * 32 + lane < tl.count) ? cnt[k] : 0u;
@@ -195,10 +209,11 @@ __global__ void k_walk(WalkArgs a)
             for (int o = 16; o > 0; o >>= 1) {
                 ci += __shfl_down_sync(FULL, ci, o);
                 cv += __shfl_down_sync(FULL, cv, o);
+                if (GROUP == 1) it = max(it, __shfl_down_sync(FULL, it, o));
             }
             if (lane == 0) {
                 atomicAdd(&sm->wstats[0], ci);
-                atomicAdd(&sm->wstats[1], (unsigned long long)iters);
+                atomicAdd(&sm->wstats[1], it);
                 atomicAdd(&sm->wstats[2], cv);
             }
         }
@@ -219,78 +234,101 @@ __global__ void k_walk(WalkArgs a)
 
 // Blocks of `warps` warps that fit on one SM, queried once per variant and
 // block size (never during stream capture: callers query before capturing).
-template <int PPL, bool KAHAN, bool POT, bool COUNT>
+template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT>
 int occupancy(int warps)
 {
     static int cache[33] = {0};
     if (warps < 1 || warps > 32) return 0;
     if (cache[warps] == 0) {
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_walk<PPL, KAHAN, POT, COUNT>,
-                                                          warps * 32, 0) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &occ, k_walk<PPL, GROUP, KAHAN, POT, COUNT>, warps * 32, 0) != cudaSuccess)
             occ = 0;
         cache[warps] = occ > 0 ? occ : -1;
     }
     return cache[warps] > 0 ? cache[warps] : 0;
 }
 
-template <int PPL, bool KAHAN, bool POT, bool COUNT>
+template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT>
 void launch_one(const WalkArgs &a, const WalkShape &sh, int nsm, cudaStream_t st)
 {
     const int threads = sh.warps * 32;
     int bps = sh.blocks_per_sm;
-    if (bps <= 0) bps = occupancy<PPL, KAHAN, POT, COUNT>(sh.warps);
+    if (bps <= 0) bps = occupancy<PPL, GROUP, KAHAN, POT, COUNT>(sh.warps);
     if (bps <= 0) bps = 1;
-    k_walk<PPL, KAHAN, POT, COUNT><<<nsm * bps, threads, 0, st>>>(a);
+    k_walk<PPL, GROUP, KAHAN, POT, COUNT><<<nsm * bps, threads, 0, st>>>(a);
 }
+
+// Dispatch of the runtime shape onto the compiled variants.
+template <bool COUNT>
+struct Variants {
+    template <int PPL, int GROUP>
+    static int pick(bool kahan, bool pot, const WalkArgs *a, const WalkShape &sh, int nsm,
+                    cudaStream_t st)
+    {
+        if (COUNT) {
+            if (a) launch_one<PPL, GROUP, true, false, true>(*a, sh, nsm, st);
+            return occupancy<PPL, GROUP, true, false, true>(sh.warps);
+        }
+        if (kahan && pot) {
+            if (a) launch_one<PPL, GROUP, true, true, false>(*a, sh, nsm, st);
+            return occupancy<PPL, GROUP, true, true, false>(sh.warps);
+        }
+        if (kahan) {
+            if (a) launch_one<PPL, GROUP, true, false, false>(*a, sh, nsm, st);
+            return occupancy<PPL, GROUP, true, false, false>(sh.warps);
+        }
+        if (pot) {
+            if (a) launch_one<PPL, GROUP, false, true, false>(*a, sh, nsm, st);
+            return occupancy<PPL, GROUP, false, true, false>(sh.warps);
+        }
+        if (a) launch_one<PPL, GROUP, false, false, false>(*a, sh, nsm, st);
+        return occupancy<PPL, GROUP, false, false, false>(sh.warps);
+    }
+
+    // returns the occupancy of the variant (0 = shape not supported)
+    static int run(bool kahan, bool pot, const WalkArgs *a, const WalkShape &sh, int nsm,
+                   cudaStream_t st)
+    {
+        if (COUNT) {
+            if (sh.ppl != 1) return 0;
+            return sh.group == 1 ? pick<1, 1>(kahan, pot, a, sh, nsm, st)
+                                 : pick<1, 32>(kahan, pot, a, sh, nsm, st);
+        }
+        if (sh.group == 32) {
+            switch (sh.ppl) {
+                case 1: return pick<1, 32>(kahan, pot, a, sh, nsm, st);
+                case 2: return pick<2, 32>(kahan, pot, a, sh, nsm, st);
+                case 4: return pick<4, 32>(kahan, pot, a, sh, nsm, st);
+            }
+        } else if (sh.group == 1) {
+            switch (sh.ppl) {
+                case 1: return pick<1, 1>(kahan, pot, a, sh, nsm, st);
+                case 2: return pick<2, 1>(kahan, pot, a, sh, nsm, st);
+            }
+        }
+        return 0;
+    }
+};
 
 }  // namespace
 
 int launch_walk(const WalkArgs &a, const WalkShape &sh, bool kahan, bool pot, bool count,
                 int nsm, cudaStream_t st)
 {
-    if (count) {
-        launch_one<1, true, false, true>(a, sh, nsm, st);
-        g_launches += 1;
-        return 1;
-    }
-#define BH_WALK_CASE(P)                                                         \
-    case P:                                                                     \
-        if (kahan) {                                                            \
-            if (pot) launch_one<P, true, true, false>(a, sh, nsm, st);          \
-            else launch_one<P, true, false, false>(a, sh, nsm, st);             \
-        } else {                                                                \
-            if (pot) launch_one<P, false, true, false>(a, sh, nsm, st);         \
-            else launch_one<P, false, false, false>(a, sh, nsm, st);            \
-        }                                                                       \
-        break;
-    switch (sh.ppl) {
-        BH_WALK_CASE(1)
-        BH_WALK_CASE(2)
-        BH_WALK_CASE(4)
-        default: return -1;
-    }
-#undef BH_WALK_CASE
+    const int occ = count ? Variants<true>::run(kahan, pot, &a, sh, nsm, st)
+                          : Variants<false>::run(kahan, pot, &a, sh, nsm, st);
+    if (occ <= 0) return -1;
     g_launches += 1;
     return 1;
 }
 
 int walk_max_blocks_per_sm(const WalkShape &sh, bool kahan, bool pot)
 {
-    occupancy<1, true, false, true>(8);  // the counting variant's shape
-#define BH_OCC_CASE(P)                                                          \
-    case P:                                                                     \
-        if (kahan) return pot ? occupancy<P, true, true, false>(sh.warps)       \
-                              : occupancy<P, true, false, false>(sh.warps);     \
-        return pot ? occupancy<P, false, true, false>(sh.warps)                \
-                   : occupancy<P, false, false, false>(sh.warps);
-    switch (sh.ppl) {
-        BH_OCC_CASE(1)
-        BH_OCC_CASE(2)
-        BH_OCC_CASE(4)
-        default: return 0;
-    }
-#undef BH_OCC_CASE
+    WalkShape cs = sh;
+    cs.ppl = 1;
+    Variants<true>::run(true, false, nullptr, cs, 0, nullptr);  // the counting variant too
+    return Variants<false>::run(kahan, pot, nullptr, sh, 0, nullptr);
 }
 
 }  // namespace bh

@@ -207,15 +207,19 @@ def test_launch_shape_does_not_change_results():
     h = make(pm, eps=0.005, theta=0.6)
     try:
         ref = None
-        for ppl in (1, 2, 4):
+        for group, ppl in ((1, 1), (1, 2), (32, 1), (32, 2), (32, 4)):
             for w in (4, 8, 16):
-                B.bh_set_tuning(h, ppl, w, 0)
+                B.bh_set_tuning(h, ppl, w, 0, group)
                 a = gpu_accel(h, 20000)
                 if ref is None:
                     ref = a
-                assert np.array_equal(a, ref), (ppl, w)
+                assert np.array_equal(a, ref), (group, ppl, w)
+                st = B.bh_walk_stats(h)
+                assert st["interactions"] <= 32 * st["warp_iterations"] * ppl
+        with pytest.raises(B.BHError):
+            B.bh_set_tuning(h, 4, 8, 0, 1)  # four particles per lane only with the warp vote
         best = B.bh_autotune(h)
-        assert best[0] in (1, 2, 4)
+        assert best[0] in (1, 2, 4) and best[3] in (1, 32)
         assert np.array_equal(gpu_accel(h, 20000), ref)
     finally:
         B.bh_destroy(h)

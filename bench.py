@@ -177,7 +177,8 @@ def run_gpu(args):
     pm, vel = synth.uniform_cube(N_PART, SEED)
     d_pm = torch.from_numpy(pm).to(dev)
     d_vel = torch.from_numpy(vel).to(dev)
-    h = B.bh_create(B.params(1.0, EPS, THETA), d_pm, d_vel, stream)
+    flags = B.BH_NO_KAHAN if args.no_kahan else 0
+    h = B.bh_create(B.params(1.0, EPS, THETA, flags), d_pm, d_vel, stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     if args.ppl:
@@ -299,7 +300,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ppl", type=int, default=0, help="fix the walk shape (skip the autotuner)")
     ap.add_argument("--warps", type=int, default=8)
-    ap.add_argument("--group", type=int, default=1, help="lanes voting together (1 or 32)")
+    ap.add_argument("--group", type=int, default=1, help="lanes voting together (1, 4, 8 or 32)")
+    ap.add_argument("--no-kahan", action="store_true", help="plain FP32 force sums")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

@@ -98,15 +98,16 @@ typedef struct bh_node {
 } bh_node;
 
 /* Walk launch shape (the autotuner's search space).
- *   ppl             particles per lane (1, 2 or 4; 1 or 2 when group is 1): a
+ *   ppl             particles per lane (1, 2 or 4; 4 only with group 32): a
  *                   warp task is a tile of 32*ppl consecutive Morton-sorted
  *                   particles
  *   warps_per_block 1..32
  *   blocks_per_sm   0 = as many as fit
- *   group           lanes that vote together on the next node: 32 = the warp
- *                   walks the union of its particles' traversals (one
- *                   broadcast node load per step), 1 = every lane walks its
- *                   own particles' traversal */
+ *   group           lanes that vote together on the next node (1, 4, 8 or
+ *                   32): 32 = the warp walks the union of its particles'
+ *                   traversals (one broadcast node load per step), 4 or 8 =
+ *                   aligned lane groups each walk their own union, 1 = every
+ *                   lane walks its own particles' traversal */
 typedef struct bh_tuning {
     int ppl;
     int warps_per_block;
@@ -151,7 +152,8 @@ int bh_set_state(bh_system *s, const float *pos_mass, const float *vel, const fl
 /* Builds the octree of the current positions (Section I; the tree-build
  * barrier of Section III): bounding cube and root centre of mass (FP64),
  * Morton keys, radix sort by (key, input index), canonical topology with the
- * depth cap, bottom-up masses and centres of mass (FP32). */
+ * depth cap, bottom-up masses and centres of mass (FP64, kept for the walk
+ * as an FP32 value plus its FP32-rounded remainder). */
 int bh_build_tree(bh_system *s);
 
 /* Copies the last built tree to host memory (for parity checks).

@@ -88,6 +88,9 @@ __device__ __forceinline__ void interact(float m, float dx, float dy, float dz, 
 
 // GROUP = 32: the warp votes (__reduce_min_sync) on the next node and visits
 // the union of its particles' traversals, one broadcast node load per step.
+// GROUP = 4, 8, 16: aligned lane groups vote among themselves (xor-shuffle
+// minimum) and each group walks the union of its own particles' traversals;
+// a warp load then touches at most 32 / GROUP nodes.
 // GROUP = 1: no vote; every lane advances through its own particles'
 // traversal (loads diverge, no lane waits on nodes it does not need).
 // Either way each particle visits exactly its own nodes in increasing index
@@ -95,7 +98,8 @@ __device__ __forceinline__ void interact(float m, float dx, float dy, float dz, 
 template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT>
 __global__ void k_walk(WalkArgs a)
 {
-    static_assert(GROUP == 1 || GROUP == 32, "vote group is a lane or the warp");
+    static_assert(GROUP == 1 || GROUP == 4 || GROUP == 8 || GROUP == 16 || GROUP == 32,
+                  "vote group: 1, 4, 8, 16 or 32 lanes");
     const int lane = threadIdx.x & 31;
     Small *sm = a.small;
     if (sm->status) return;
@@ -138,8 +142,19 @@ __global__ void k_walk(WalkArgs a)
             int cur = nxt[0];
 #pragma unroll
             for (int k = 1; k < PPL; ++k) cur = min(cur, nxt[k]);
-            if (GROUP == 32) cur = (int)__reduce_min_sync(FULL, (unsigned)cur);
-            if (cur >= nend) break;
+            if (GROUP == 32) {
+                cur = (int)__reduce_min_sync(FULL, (unsigned)cur);
+                if (cur >= nend) break;
+            } else if (GROUP > 1) {
+#pragma unroll
+                for (int o = GROUP / 2; o > 0; o >>= 1) cur = min(cur, __shfl_xor_sync(FULL, cur, o));
+                // every lane keeps executing the shuffles until the whole warp is done
+                const bool done = cur >= nend;
+                if (__all_sync(FULL, done)) break;
+                if (done) continue;
+            } else {
+                if (cur >= nend) break;
+            }
             if (COUNT) {
                 ++iters;
 #pragma unroll
@@ -209,7 +224,7 @@ __global__ void k_walk(WalkArgs a)
             for (int o = 16; o > 0; o >>= 1) {
                 ci += __shfl_down_sync(FULL, ci, o);
                 cv += __shfl_down_sync(FULL, cv, o);
-                if (GROUP == 1) it = max(it, __shfl_down_sync(FULL, it, o));
+                if (GROUP < 32) it = max(it, __shfl_down_sync(FULL, it, o));
             }
             if (lane == 0) {
                 atomicAdd(&sm->wstats[0], ci);
@@ -292,20 +307,25 @@ struct Variants {
     {
         if (COUNT) {
             if (sh.ppl != 1) return 0;
-            return sh.group == 1 ? pick<1, 1>(kahan, pot, a, sh, nsm, st)
-                                 : pick<1, 32>(kahan, pot, a, sh, nsm, st);
-        }
-        if (sh.group == 32) {
-            switch (sh.ppl) {
-                case 1: return pick<1, 32>(kahan, pot, a, sh, nsm, st);
-                case 2: return pick<2, 32>(kahan, pot, a, sh, nsm, st);
-                case 4: return pick<4, 32>(kahan, pot, a, sh, nsm, st);
-            }
-        } else if (sh.group == 1) {
-            switch (sh.ppl) {
+            switch (sh.group) {
                 case 1: return pick<1, 1>(kahan, pot, a, sh, nsm, st);
-                case 2: return pick<2, 1>(kahan, pot, a, sh, nsm, st);
+                case 4: return pick<1, 4>(kahan, pot, a, sh, nsm, st);
+                case 8: return pick<1, 8>(kahan, pot, a, sh, nsm, st);
+                case 32: return pick<1, 32>(kahan, pot, a, sh, nsm, st);
             }
+            return 0;
+        }
+        const int key = sh.group * 8 + sh.ppl;
+        switch (key) {
+            case 1 * 8 + 1: return pick<1, 1>(kahan, pot, a, sh, nsm, st);
+            case 1 * 8 + 2: return pick<2, 1>(kahan, pot, a, sh, nsm, st);
+            case 4 * 8 + 1: return pick<1, 4>(kahan, pot, a, sh, nsm, st);
+            case 4 * 8 + 2: return pick<2, 4>(kahan, pot, a, sh, nsm, st);
+            case 8 * 8 + 1: return pick<1, 8>(kahan, pot, a, sh, nsm, st);
+            case 8 * 8 + 2: return pick<2, 8>(kahan, pot, a, sh, nsm, st);
+            case 32 * 8 + 1: return pick<1, 32>(kahan, pot, a, sh, nsm, st);
+            case 32 * 8 + 2: return pick<2, 32>(kahan, pot, a, sh, nsm, st);
+            case 32 * 8 + 4: return pick<4, 32>(kahan, pot, a, sh, nsm, st);
         }
         return 0;
     }

@@ -95,7 +95,19 @@ def test_tree_bit_exact_and_accel(kind, n, seed):
         a = gpu_accel(h, n)
         T = check_tree(h, pm)
         ref, _, cnt = T.accel(theta, eps)
-        assert_accel_close(a, ref, what=f"{kind} n={n}")
+        if kind == "line":
+            # Collinear points feel nearly balanced pulls: the 99th-percentile
+            # particle's net force is ~1/940 of the sum of its terms' sizes, so
+            # FP32 rounding of the terms alone exceeds 1e-5 of |a|.  Here the
+            # error is measured against that sum (as for the theta = 0 gate).
+            x, m = pm[:, :3].astype(np.float64), pm[:, 3].astype(np.float64)
+            d = x[None, :, :] - x[:, None, :]
+            r2 = (d ** 2).sum(-1) + eps ** 2
+            mag = (m[None, :] * np.sqrt((d ** 2).sum(-1)) / r2 ** 1.5).sum(1)
+            e = np.linalg.norm(a[:, :3] - ref, axis=1) / mag
+            assert np.percentile(e, 99) <= 1e-6 and e.max() <= 1e-5, (np.percentile(e, 99), e.max())
+        else:
+            assert_accel_close(a, ref, what=f"{kind} n={n}")
         gc, tot = B.bh_interaction_count(h, n)
         # opening decisions near a tie are re-taken in FP64: counts are exact
         mism = np.count_nonzero(gc.astype(np.int64) != cnt)
@@ -207,7 +219,7 @@ def test_launch_shape_does_not_change_results():
     h = make(pm, eps=0.005, theta=0.6)
     try:
         ref = None
-        for group, ppl in ((1, 1), (1, 2), (32, 1), (32, 2), (32, 4)):
+        for group, ppl in ((1, 1), (1, 2), (4, 1), (4, 2), (8, 1), (8, 2), (32, 1), (32, 2), (32, 4)):
             for w in (4, 8, 16):
                 B.bh_set_tuning(h, ppl, w, 0, group)
                 a = gpu_accel(h, 20000)

@@ -14,21 +14,11 @@
 //     virtual ids (double-buffered for the radix sort), the Morton-ordered
 //     copy spos of pos_mass, per-particle node counts / offsets.
 //   * Nodes of all trees in one array, each system's nodes contiguous, in
-//     depth-first pre-order (the canonical order).  The walk's record WNode
-//     (48 bytes, one array so a lane's three loads share two sectors) is
-//       a = (hx, hy, hz, mass)   FP32 centre of mass (high part), mass
-//       b = (lx, ly, lz, crit2)  low part (com - h rounded to FP32) and
-//                                    the opening threshold s^2/theta^2
-//                                    (accept iff d^2 > crit2); -1 for a
-//                                    one-particle leaf (always taken as is),
-//                                    -2 for a depth-cap bucket (particles one
-//                                    by one)
-//       c = (skip, first, count, level)  skip = index of the next node
-//                                    after the subtree
-//     and a separate FP64 array nodeD = (mass, cx, cy, cz), for the
-//     bottom-up pass and for
-//                                    re-deciding opening tests that fall
-//                                    within rounding distance of a tie
+//     depth-first pre-order (the canonical order): the 32-byte walk record
+//     WNode (below), the rarely used fields nodeR = (first, count, level, 0)
+//     and the FP64 centre of mass nodeD = (mass, cx, cy, cz), which the
+//     bottom-up pass works in and the walk reads only to re-decide opening
+//     tests that fall within rounding distance of a tie.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -104,11 +94,49 @@ struct Small {
     unsigned level_off[kNumLevels + 1];
 };
 
-struct __align__(16) WNode {
+// The walk's node record: 32 bytes, one DRAM/L2 sector.
+//   a = (hx, hy, hz, mass)   FP32 centre of mass (high part) and mass
+//   b = (crit2 bits, skip, lo_xy, lo_z | e << 16)
+//       crit2 = s^2/theta^2 (accept iff d^2 > crit2), -1 for a one-particle
+//       leaf (always taken as is), -2 for a depth-cap bucket; skip = index of
+//       the next node after the subtree; the low part com - h of each
+//       coordinate as an int16 multiple of 2^(e - 127) (e chosen per node
+//       from the largest |h|, so the low part keeps 2^-16 of an FP32 ulp).
+// Fields the walk rarely needs live in nodeR = (first, count, level, 0).
+struct __align__(32) WNode {
     float4 a;
-    float4 b;
-    int4 c;
+    uint4 b;
 };
+
+#ifdef __CUDACC__
+__device__ __forceinline__ float wn_crit(const uint4 &b) { return __uint_as_float(b.x); }
+__device__ __forceinline__ int wn_skip(const uint4 &b) { return (int)b.y; }
+
+__device__ __forceinline__ void wn_lo(const uint4 &b, float &lx, float &ly, float &lz)
+{
+    const float scale = __int_as_float((int)(b.w >> 16) << 23);
+    lx = (float)(short)(b.z & 0xffffu) * scale;
+    ly = (float)(short)(b.z >> 16) * scale;
+    lz = (float)(short)(b.w & 0xffffu) * scale;
+}
+
+// Packs threshold, skip pointer and the low parts com - h (FP64) of a node.
+__device__ __forceinline__ uint4 wn_pack(float crit, int skip, double cx, double cy, double cz,
+                                         float hx, float hy, float hz)
+{
+    const float mx = fmaxf(fabsf(hx), fmaxf(fabsf(hy), fabsf(hz)));
+    // |com - h| <= ulp(mx)/2 = 2^(E-151); the scale 2^(E-165) keeps |q| <= 2^14
+    int e = ((__float_as_int(mx) >> 23) & 0xff) - 38;
+    if (e < 1) e = 1;
+    const double inv = __longlong_as_double((long long)(1023 - (e - 127)) << 52);
+    const int qx = max(-32767, min(32767, __double2int_rn((cx - (double)hx) * inv)));
+    const int qy = max(-32767, min(32767, __double2int_rn((cy - (double)hy) * inv)));
+    const int qz = max(-32767, min(32767, __double2int_rn((cz - (double)hz) * inv)));
+    return make_uint4(__float_as_uint(crit), (unsigned)skip,
+                      ((unsigned)qx & 0xffffu) | ((unsigned)qy << 16),
+                      ((unsigned)qz & 0xffffu) | ((unsigned)e << 16));
+}
+#endif
 
 struct Tile {
     int start;  // virtual index of the first particle (sorted order)
@@ -135,6 +163,7 @@ struct BuildBufs {
     uint32_t *ncount;     // n_total + 1
     uint32_t *noff;       // n_total + 1
     WNode *nodeW;
+    int4 *nodeR;
     double4 *nodeD;
     uint32_t *nlist;
     unsigned node_cap;
@@ -162,6 +191,7 @@ void launch_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *partials,
 
 struct WalkArgs {
     const WNode *nodeW;
+    const int4 *nodeR;
     const double4 *nodeD;
     const SysDyn *dyn;
     const float4 *spos;

@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(kChunkThreads)
 k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
              const SysDyn *__restrict__ dyn, const uint64_t *__restrict__ key,
              const uint32_t *__restrict__ noff, const float4 *__restrict__ spos,
-             WNode *__restrict__ nodeW, double4 *__restrict__ nodeD,
+             WNode *__restrict__ nodeW, int4 *__restrict__ nodeR, double4 *__restrict__ nodeD,
              uint32_t *__restrict__ nlist, Small *__restrict__ sm)
 {
     if (halted(sm)) return;
@@ -412,8 +412,9 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
                 const float sl = __fmul_rn(D.side, pow2_neg(l));
                 crit = __fmul_rn(__fmul_rn(sl, sl), S.inv_theta2);
             }
-            nodeW[n].c = make_int4((int)noff[end], j, count, l);
-            nodeW[n].b = make_float4(0.f, 0.f, 0.f, crit);
+            nodeR[n] = make_int4(j, count, l, 0);
+            // low part 0 with scale 2^0 until the centre-of-mass pass fills it
+            nodeW[n].b = make_uint4(__float_as_uint(crit), noff[end], 0u, 127u << 16);
             nlist[base[l] + atomicAdd(&h[l], 1u)] = n;
             if (l == 0) {
                 if (count == 1) {
@@ -424,7 +425,7 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
                     const double cx = D.mx[0] / D.mtot, cy = D.mx[1] / D.mtot, cz = D.mx[2] / D.mtot;
                     const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
                     nodeW[n].a = make_float4(hx, hy, hz, (float)D.mtot);
-                    nodeW[n].b = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), crit);
+                    nodeW[n].b = wn_pack(crit, (int)noff[end], cx, cy, cz, hx, hy, hz);
                     nodeD[n] = make_double4(D.mtot, cx, cy, cz);
                 }
             }
@@ -441,24 +442,27 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
 // split into an FP32 high part and the FP32-rounded remainder for the walk.
 __global__ void __launch_bounds__(256)
 k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
-            WNode *__restrict__ nodeW, double4 *__restrict__ nodeD, const Small *__restrict__ sm)
+            WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4 *__restrict__ nodeD,
+            const Small *__restrict__ sm)
 {
     if (halted(sm)) return;
     const unsigned cnt = sm->level_cnt[l];
     const unsigned off = sm->level_off[l];
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
         const unsigned n = nlist[off + k];
-        const int4 C = nodeW[n].c;
-        const float crit = nodeW[n].b.w;
+        const int4 C = nodeR[n];  // first, count, level
+        const uint4 B = nodeW[n].b;
+        const float crit = wn_crit(B);
+        const int skip = wn_skip(B);
         if (crit == kLeafCrit) {
-            const float4 p = spos[C.y];
+            const float4 p = spos[C.x];
             nodeW[n].a = p;
             nodeD[n] = make_double4(p.w, p.x, p.y, p.z);
             continue;
         }
         double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
         if (crit == kBucketCrit) {
-            for (int q = C.y; q < C.y + C.z; ++q) {
+            for (int q = C.x; q < C.x + C.y; ++q) {
                 const float4 p = spos[q];
                 const double m = p.w;
                 M += m;
@@ -467,7 +471,7 @@ k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict_
                 sz += m * (double)p.z;
             }
         } else {
-            for (int ch = (int)n + 1; ch < C.x; ch = nodeW[ch].c.x) {
+            for (int ch = (int)n + 1; ch < skip; ch = wn_skip(nodeW[ch].b)) {
                 const double4 d = nodeD[ch];
                 M += d.x;
                 sx += d.x * d.y;
@@ -479,7 +483,7 @@ k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict_
         const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
         nodeD[n] = make_double4(M, cx, cy, cz);
         nodeW[n].a = make_float4(hx, hy, hz, (float)M);
-        nodeW[n].b = make_float4((float)(cx - hx), (float)(cy - hy), (float)(cz - hz), crit);
+        nodeW[n].b = wn_pack(crit, skip, cx, cy, cz, hx, hy, hz);
     }
 }
 
@@ -610,27 +614,29 @@ __global__ void k_diag_final(const SysStatic *__restrict__ sys, const DiagPart *
 __global__ void __launch_bounds__(256)
 k_export(int sysid, const SysStatic *__restrict__ sys, const uint32_t *__restrict__ noff,
          const uint64_t *__restrict__ key, const uint32_t *__restrict__ sid,
-         const WNode *__restrict__ nodeW, bh_node *__restrict__ out_nodes,
+         const WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR,
+         bh_node *__restrict__ out_nodes,
          float4 *__restrict__ out_com, uint32_t *__restrict__ out_order)
 {
     const SysStatic S = sys[sysid];
     const unsigned n0 = noff[S.start], n1 = noff[S.start + S.n];
     const unsigned stride = gridDim.x * blockDim.x;
     for (unsigned n = n0 + blockIdx.x * blockDim.x + threadIdx.x; n < n1; n += stride) {
-        const int4 C = nodeW[n].c;
-        const int l = C.w;
-        const uint64_t pre = (l == 0) ? 0ull : (key[C.y] >> (3 * (kLevels - l)));
+        const int4 C = nodeR[n];  // first, count, level
+        const int l = C.z;
+        const uint64_t pre = (l == 0) ? 0ull : (key[C.x] >> (3 * (kLevels - l)));
         unsigned cm = 0;
-        const float4 B = nodeW[n].b;
-        if (B.w != kLeafCrit && B.w != kBucketCrit) {
-            for (int ch = (int)n + 1; ch < C.x; ch = nodeW[ch].c.x)
-                cm |= 1u << (unsigned)((key[nodeW[ch].c.y] >> (3 * (kLevels - l - 1))) & 7u);
+        const uint4 B = nodeW[n].b;
+        const float crit = wn_crit(B);
+        if (crit != kLeafCrit && crit != kBucketCrit) {
+            for (int ch = (int)n + 1; ch < wn_skip(B); ch = wn_skip(nodeW[ch].b))
+                cm |= 1u << (unsigned)((key[nodeR[ch].x] >> (3 * (kLevels - l - 1))) & 7u);
         }
         if (out_nodes) {
             bh_node o;
             o.prefix = pre;
-            o.first = (uint32_t)(C.y - S.start);
-            o.count = (uint32_t)C.z;
+            o.first = (uint32_t)(C.x - S.start);
+            o.count = (uint32_t)C.y;
             o.level = (uint8_t)l;
             o.childmask = (uint8_t)cm;
             for (int q = 0; q < 6; ++q) o.pad[q] = 0;
@@ -638,7 +644,9 @@ k_export(int sysid, const SysStatic *__restrict__ sys, const uint32_t *__restric
         }
         if (out_com) {
             const float4 A = nodeW[n].a;
-            out_com[n - n0] = make_float4(A.x + B.x, A.y + B.y, A.z + B.z, A.w);
+            float lx, ly, lz;
+            wn_lo(B, lx, ly, lz);
+            out_com[n - n0] = make_float4(A.x + lx, A.y + ly, A.z + lz, A.w);
         }
     }
     if (out_order) {
@@ -677,7 +685,8 @@ void launch_topology(const BuildBufs &b, cudaStream_t st)
     launch_scan(b.ncount, b.noff, b.n_total, b.scan_part, b.noff + b.n_total, &b.small->status, st);
     k_level_offsets<<<1, 32, 0, st>>>(b.small, b.noff, b.n_total, b.node_cap);
     k_topo_write<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.dyn, b.key0, b.noff,
-                                                      b.spos, b.nodeW, b.nodeD, b.nlist, b.small);
+                                                      b.spos, b.nodeW, b.nodeR, b.nodeD, b.nlist,
+                                                      b.small);
     g_launches += 2;
 }
 
@@ -685,7 +694,7 @@ void launch_com(const BuildBufs &b, cudaStream_t st)
 {
     const int grid = b.nsm * 8;
     for (int l = kLevels; l >= 1; --l) {
-        k_com_level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeW, b.nodeD, b.small);
+        k_com_level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeW, b.nodeR, b.nodeD, b.small);
         g_launches += 1;
     }
 }
@@ -718,7 +727,7 @@ void launch_diagnostics(const BuildBufs &b, DiagPart *parts, double *out, cudaSt
 void launch_export(const BuildBufs &b, int sysid, bh_node *nodes_dev, float4 *com_dev,
                    uint32_t *order_dev, cudaStream_t st)
 {
-    k_export<<<b.nsm * 4, 256, 0, st>>>(sysid, b.sys, b.noff, b.key0, b.val0, b.nodeW,
+    k_export<<<b.nsm * 4, 256, 0, st>>>(sysid, b.sys, b.noff, b.key0, b.val0, b.nodeW, b.nodeR,
                                         nodes_dev, com_dev, order_dev);
     g_launches += 1;
 }

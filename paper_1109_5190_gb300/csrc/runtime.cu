@@ -183,7 +183,7 @@ struct Forest {
     bool tables_dirty = true;
 
     DevBuf d_sys, d_dyn, d_chunks, d_mode, d_parts, key0, key1, val0, val1, rs_counts, scan_part,
-        spos, ncount, noff, nodeW, nodeD, nlist, d_small, d_diag_parts, d_diag_out,
+        spos, ncount, noff, nodeW, nodeR, nodeD, nlist, d_small, d_diag_parts, d_diag_out,
         d_counts, d_export;
     unsigned node_cap = 0;
     struct TileSet {
@@ -272,6 +272,7 @@ struct Forest {
         b.ncount = ncount.as<uint32_t>();
         b.noff = noff.as<uint32_t>();
         b.nodeW = nodeW.as<WNode>();
+        b.nodeR = nodeR.as<int4>();
         b.nodeD = nodeD.as<double4>();
         b.nlist = nlist.as<uint32_t>();
         b.node_cap = node_cap;
@@ -285,6 +286,7 @@ struct Forest {
     {
         if (cap <= node_cap && nodeW.p) return BH_OK;
         TRY(nodeW.ensure(cap * sizeof(WNode)));
+        TRY(nodeR.ensure(cap * sizeof(int4)));
         TRY(nodeD.ensure(cap * sizeof(double4)));
         TRY(nlist.ensure(cap * sizeof(uint32_t)));
         node_cap = (unsigned)cap;
@@ -423,6 +425,7 @@ struct Forest {
     {
         WalkArgs a;
         a.nodeW = nodeW.as<WNode>();
+        a.nodeR = nodeR.as<int4>();
         a.nodeD = nodeD.as<double4>();
         a.dyn = d_dyn.as<SysDyn>();
         a.spos = spos.as<float4>();

@@ -57,9 +57,11 @@ __device__ __forceinline__ void acc_add(float &s, float &c, float x)
 // rounding distance of the threshold: s^2 < theta^2 d^2 with s = side 2^-level
 // and d from the FP64 centre of mass (the same formula and operation order as
 // the FP64 definition, so both decide alike).
-__device__ __noinline__ bool accept_fp64(const double4 *__restrict__ nodeD, int node, int level,
-                                         float px, float py, float pz, double side, double theta2)
+__device__ __noinline__ bool accept_fp64(const double4 *__restrict__ nodeD,
+                                         const int4 *__restrict__ nodeR, int node, float px,
+                                         float py, float pz, double side, double theta2)
 {
+    const int level = nodeR[node].z;
     const double4 D = nodeD[node];
     const double dx = __dsub_rn(D.y, (double)px);
     const double dy = __dsub_rn(D.z, (double)py);
@@ -162,15 +164,16 @@ __global__ void k_walk(WalkArgs a)
             }
             const WNode *np = a.nodeW + cur;
             const float4 A = __ldg(&np->a);
-            const float4 Bf = __ldg(&np->b);
-            const int4 C = __ldg(&np->c);
-            if (C.x <= cur) {  // corrupt skip pointer: report, never spin
+            const uint4 B = __ldg(&np->b);
+            const int skip = wn_skip(B);
+            if (skip <= cur) {  // corrupt skip pointer: report, never spin
                 atomicExch(&sm->status, ST_WALK_LIMIT);
                 break;
             }
-            const float crit = Bf.w;
+            const float crit = wn_crit(B);
             if (crit == kBucketCrit) {
-                for (int q = C.y; q < C.y + C.z; ++q) {
+                const int4 R = __ldg(&a.nodeR[cur]);  // first, count
+                for (int q = R.x; q < R.x + R.y; ++q) {
                     const float4 P = __ldg(&a.spos[q]);
 #pragma unroll
                     for (int k = 0; k < PPL; ++k) {
@@ -185,27 +188,31 @@ __global__ void k_walk(WalkArgs a)
                 }
 #pragma unroll
                 for (int k = 0; k < PPL; ++k)
-                    if (nxt[k] == cur) nxt[k] = C.x;
+                    if (nxt[k] == cur) nxt[k] = skip;
             } else {
                 const float band = crit * kTieBand;  // negative for leaves: never a tie
+                float lx, ly, lz;
+                wn_lo(B, lx, ly, lz);
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
                     if (nxt[k] == cur) {
-                        // distance to the centre of mass from its high and low FP32 parts
-                        const float dx = (A.x - px[k]) + Bf.x;
-                        const float dy = (A.y - py[k]) + Bf.y;
-                        const float dz = (A.z - pz[k]) + Bf.z;
+                        // distance to the centre of mass from its high and low parts
+                        const float dx = (A.x - px[k]) + lx;
+                        const float dy = (A.y - py[k]) + ly;
+                        const float dz = (A.z - pz[k]) + lz;
                         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         const float diff = d2 - crit;
                         bool acc = diff > 0.f;
                         if (fabsf(diff) < band)
-                            acc = accept_fp64(a.nodeD, cur, C.w, px[k], py[k], pz[k], side, theta2);
+                            acc = accept_fp64(a.nodeD, a.nodeR, cur, px[k], py[k], pz[k], side,
+                                              theta2);
                         if (acc) {
-                            interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2,
-                                                        crit == kLeafCrit && C.y == myj[k],
+                            // the potential leaves out the particle's own leaf
+                            const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[cur].x) == myj[k];
+                            interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self,
                                                         ax[k], ay[k], az[k], cx[k], cy[k], cz[k],
                                                         pp[k], cp[k], cnt[k]);
-                            nxt[k] = C.x;
+                            nxt[k] = skip;
                         } else {
                             nxt[k] = cur + 1;
                         }
@@ -255,6 +262,9 @@ int occupancy(int warps)
     static int cache[33] = {0};
     if (warps < 1 || warps > 32) return 0;
     if (cache[warps] == 0) {
+        // the walk uses no shared memory: give the SM's unified storage to L1
+        cudaFuncSetAttribute(k_walk<PPL, GROUP, KAHAN, POT, COUNT>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, 0);
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &occ, k_walk<PPL, GROUP, KAHAN, POT, COUNT>, warps * 32, 0) != cudaSuccess)

@@ -101,9 +101,9 @@ typedef struct bh_node {
  *   ppl             particles per lane (1, 2 or 4; 4 only with group 32): a
  *                   warp task is a tile of 32*ppl consecutive Morton-sorted
  *                   particles
- *   warps_per_block 1..32
+ *   warps_per_block 1..16
  *   blocks_per_sm   0 = as many as fit
- *   group           lanes that vote together on the next node (1, 4, 8 or
+ *   group           lanes that vote together on the next node (1, 2, 4, 8 or
  *                   32): 32 = the warp walks the union of its particles'
  *                   traversals (one broadcast node load per step), 4 or 8 =
  *                   aligned lane groups each walk their own union, 1 = every

@@ -97,11 +97,16 @@ __device__ __forceinline__ void interact(float m, float dx, float dy, float dz, 
 // traversal (loads diverge, no lane waits on nodes it does not need).
 // Either way each particle visits exactly its own nodes in increasing index
 // order, so its sums -- and the results -- do not depend on the shape.
+// Register budget: a block of up to 512 threads, and enough blocks per SM
+// for 48 resident warps with one particle per lane.
 template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT>
-__global__ void k_walk(WalkArgs a)
+__global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
 {
-    static_assert(GROUP == 1 || GROUP == 4 || GROUP == 8 || GROUP == 16 || GROUP == 32,
-                  "vote group: 1, 4, 8, 16 or 32 lanes");
+    static_assert(GROUP == 1 || GROUP == 2 || GROUP == 4 || GROUP == 8 || GROUP == 16 ||
+                      GROUP == 32,
+                  "vote group: 1, 2, 4, 8, 16 or 32 lanes");
+    // a lone particle per lane that walks alone is always the one at `cur`
+    constexpr bool kSolo = PPL == 1 && GROUP == 1;
     const int lane = threadIdx.x & 31;
     Small *sm = a.small;
     if (sm->status) return;
@@ -177,7 +182,7 @@ __global__ void k_walk(WalkArgs a)
                     const float4 P = __ldg(&a.spos[q]);
 #pragma unroll
                     for (int k = 0; k < PPL; ++k) {
-                        if (nxt[k] == cur) {
+                        if (kSolo || nxt[k] == cur) {
                             const float dx = P.x - px[k], dy = P.y - py[k], dz = P.z - pz[k];
                             const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                             interact<KAHAN, POT, COUNT>(P.w, dx, dy, dz, d2, eps2, q == myj[k],
@@ -188,14 +193,14 @@ __global__ void k_walk(WalkArgs a)
                 }
 #pragma unroll
                 for (int k = 0; k < PPL; ++k)
-                    if (nxt[k] == cur) nxt[k] = skip;
+                    if (kSolo || nxt[k] == cur) nxt[k] = skip;
             } else {
                 const float band = crit * kTieBand;  // negative for leaves: never a tie
                 float lx, ly, lz;
                 wn_lo(B, lx, ly, lz);
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
-                    if (nxt[k] == cur) {
+                    if (kSolo || nxt[k] == cur) {
                         // distance to the centre of mass from its high and low parts
                         const float dx = (A.x - px[k]) + lx;
                         const float dy = (A.y - py[k]) + ly;
@@ -319,6 +324,7 @@ struct Variants {
             if (sh.ppl != 1) return 0;
             switch (sh.group) {
                 case 1: return pick<1, 1>(kahan, pot, a, sh, nsm, st);
+                case 2: return pick<1, 2>(kahan, pot, a, sh, nsm, st);
                 case 4: return pick<1, 4>(kahan, pot, a, sh, nsm, st);
                 case 8: return pick<1, 8>(kahan, pot, a, sh, nsm, st);
                 case 32: return pick<1, 32>(kahan, pot, a, sh, nsm, st);
@@ -329,6 +335,7 @@ struct Variants {
         switch (key) {
             case 1 * 8 + 1: return pick<1, 1>(kahan, pot, a, sh, nsm, st);
             case 1 * 8 + 2: return pick<2, 1>(kahan, pot, a, sh, nsm, st);
+            case 2 * 8 + 1: return pick<1, 2>(kahan, pot, a, sh, nsm, st);
             case 4 * 8 + 1: return pick<1, 4>(kahan, pot, a, sh, nsm, st);
             case 4 * 8 + 2: return pick<2, 4>(kahan, pot, a, sh, nsm, st);
             case 8 * 8 + 1: return pick<1, 8>(kahan, pot, a, sh, nsm, st);

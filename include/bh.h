@@ -306,6 +306,31 @@ double bh_server_now(bh_server *s);
 /* Stops the thread; pending and running requests end with BH_ERR_CANCELLED. */
 int bh_server_destroy(bh_server *s);
 
+/* ------------------------------------------------- allocation-free Morton keys */
+
+/* The paper has no counterpart to this call: it exists for callers that
+ * cannot allocate device memory.  cudaMalloc may wait until the whole device
+ * is idle and fails when another allocator (a framework's caching allocator,
+ * a pre-carved pool) already holds the free memory; code on a latency-critical
+ * loop, or code that owns no allocator, can still compute keys here.
+ *
+ * Computes, for n particles (pos_mass: device, n x 4 floats), the same 63-bit
+ * Morton keys as the tree build (keys: device, n uint64, input order) and the
+ * key cube (cube: device, 4 floats lo_x, lo_y, lo_z, side; may be NULL).
+ * Allocates nothing and calls no allocating routine: its only scratch is a
+ * file-scope device array of 128 KiB + 32 bytes (per-chunk boxes), held on
+ * every GPU that loads the library until the process exits.  n must be in
+ * [1, BH_NOALLOC_MAX_N]; larger n returns BH_ERR_INVALID with a message.
+ * The work is enqueued on `stream` (NULL = legacy default stream) and the call
+ * returns without synchronising.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call on a device
+ * shares its array and overwrites what it reads, so calls whose work
+ * overlaps on one GPU race: keep them on one stream or order them. */
+#define BH_NOALLOC_MAX_N 16777216
+int bh_morton_keys_noalloc(const float *pos_mass, int64_t n, uint64_t *keys, float *cube,
+                           void *stream);
+
 /* ---------------------------------------------------------- micro-benchmarks */
 
 /* Measured FP32 non-tensor throughput: a kernel of independent FMA chains on

@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbh.so")
 
-SOURCES = ["build_kernels.cu", "sort_scan.cu", "walk.cu", "micro.cu", "runtime.cu"]
+SOURCES = ["build_kernels.cu", "sort_scan.cu", "walk.cu", "micro.cu", "runtime.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
            "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

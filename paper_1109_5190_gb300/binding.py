@@ -115,6 +115,7 @@ _SIGS = {
     "bh_server_stats_get": ([P, P], I),
     "bh_server_now": ([P], D),
     "bh_server_destroy": ([P], I),
+    "bh_morton_keys_noalloc": ([P, I64, P, P, P], I),
     "bh_micro_fma_peak": ([P, P], I),
     "bh_micro_copy_bw": ([SZ, P, P], I),
 }
@@ -412,6 +413,25 @@ def bh_server_now(h) -> float:
 
 def bh_server_destroy(h):
     return _check(lib.bh_server_destroy(h))
+
+
+# ------------------------------------------------- allocation-free Morton keys
+
+BH_NOALLOC_MAX_N = 16777216
+
+
+def bh_morton_keys_noalloc(pos_mass, keys, cube=None, stream=None):
+    """Keys of device pos_mass (n x 4 float32) into device keys (n int64 /
+    uint64 tensor) and cube (4 float32 or None); enqueued on `stream`, no
+    allocation.  For callers that cannot allocate device memory."""
+    n = pos_mass.numel() // 4
+    if not (_is_torch(pos_mass) and pos_mass.is_cuda and _is_torch(keys) and keys.is_cuda):
+        raise ValueError("device tensors required")
+    if keys.numel() != n or keys.element_size() != 8:
+        raise ValueError("keys must hold n 64-bit values")
+    cp = C.c_void_p(cube.data_ptr()) if cube is not None else None
+    return _check(lib.bh_morton_keys_noalloc(C.c_void_p(pos_mass.data_ptr()), n,
+                                             C.c_void_p(keys.data_ptr()), cp, _stream(stream)))
 
 
 # ---------------------------------------------------------- micro-benchmarks

@@ -1461,3 +1461,8 @@ int bh_server_destroy(bh_server *s)
 }
 
 }  // extern "C"
+
+namespace bh {
+// Lets other translation units report through bh_last_error().
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace bh

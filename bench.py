@@ -187,8 +187,11 @@ def run_gpu(args):
     else:
         tuning = B.bh_autotune(h)
     B.bh_compute_accel(h)
+    graph = not args.no_graph
+    B.bh_profile_begin(h)  # the captured step then carries its phase events
     for _ in range(args.warmup):
-        B.bh_step(h, 1, DT)
+        B.bh_step(h, 1, DT, graph)
+    B.bh_profile_end(h)
     ws0 = B.bh_walk_stats(h)
     inter0 = ws0["interactions"]
 
@@ -202,7 +205,7 @@ def run_gpu(args):
     for _ in range(args.steps):
         flush.fill_(1)
         torch.cuda.synchronize()
-        B.bh_step(h, 1, DT)
+        B.bh_step(h, 1, DT, graph)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     phase_ms, nsteps, launches = B.bh_profile_end(h)
@@ -248,6 +251,11 @@ def run_gpu(args):
                "h2d_bytes_per_step": 3 * N_PART * 16, "d2h_bytes_per_step": 3 * N_PART * 16}
 
     B.bh_destroy(h)
+    extra = {}
+    if rank == 0 and not args.no_batched:
+        extra["batched"] = bench_batched(args, B, torch)
+    if rank == 0 and not args.no_served:
+        extra["served"] = bench_served(args, B, torch)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -275,6 +283,7 @@ def run_gpu(args):
         "clocks": clocks,
         "gpu_launches": launches,
     }
+    line.update(extra)
     if rank == 0 and ws == 1 and not args.no_cpu:
         v, spent, threads = cpu_sample(pm, args.cpu_sample)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -286,6 +295,108 @@ def run_gpu(args):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def bench_batched(args, B, torch):
+    """Forest of many uneven systems (N log-uniform in [256, 65536], half
+    Plummer, half uniform cold collapse, eps 0.01, theta 0.5, dt 1e-3): all
+    steps of one call in one CUDA graph, one persistent walk per step across
+    all trees; against the plain single-system path solving the same systems
+    one after another."""
+    import synth
+    systems = synth.forest_systems(args.forest_systems, 256, 65536, seed=4, theta=0.5, eps=0.01)
+    n_tot = sum(s.n for s in systems)
+    descs = [dict(pos_mass=s.pos_mass, vel=s.vel, eps=s.eps, theta=s.theta, dt=1e-3) for s in systems]
+    f = B.bh_forest_create(descs)
+    try:
+        B.bh_forest_compute_accel(f)
+        shape = B.bh_forest_autotune(f)
+        B.bh_forest_step(f, args.forest_steps, 1e-3, True)  # capture + warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.bh_forest_step(f, args.forest_steps, 1e-3, True)
+        torch.cuda.synchronize()
+        t_forest = time.perf_counter() - t0
+        _, nodes = B.bh_forest_info(f)
+    finally:
+        B.bh_forest_destroy(f)
+    batched = n_tot * args.forest_steps / t_forest
+    # the plain path, one system after another (device time of bh_step only)
+    t_plain, ps_plain = 0.0, 0
+    for s in systems:
+        h = B.bh_create(B.params(1.0, s.eps, s.theta), s.pos_mass, s.vel)
+        try:
+            B.bh_compute_accel(h)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.bh_step(h, args.plain_steps, 1e-3)
+            t_plain += time.perf_counter() - t0
+            ps_plain += s.n * args.plain_steps
+        finally:
+            B.bh_destroy(h)
+    plain = ps_plain / t_plain
+    return {"workload": f"{len(systems)} systems, N log-uniform [256, 65536] (sum {n_tot}), "
+                        "half Plummer / half uniform cold collapse, eps 0.01, theta 0.5, dt 1e-3, seed 4",
+            "value": batched, "unit": UNIT, "steps_in_one_graph": args.forest_steps,
+            "ms_per_step": 1e3 * t_forest / args.forest_steps, "nodes": nodes,
+            "walk_shape": list(shape),
+            "plain_sequential": {"value": plain, "unit": UNIT,
+                                 "steps_per_system": args.plain_steps,
+                                 "how": "bh_step on each system in turn, kernels launched directly"},
+            "speedup_vs_plain": batched / plain}
+
+
+def bench_served(args, B, torch):
+    """Poisson request stream (200 requests/s; each request a Plummer or
+    uniform system of N log-uniform in [1024, 2097152], theta U[0.5, 0.8],
+    10-200 KDK steps of dt 1e-3, eps 0.01) through bh_submit / bh_wait, with
+    continuous batching under a 160 GB HBM budget.  Particles of a request are
+    a seeded random subset of a pre-drawn 2^21-particle Plummer sphere or
+    uniform cube, masses 1/N (a random subset of independent draws is itself
+    an independent draw)."""
+    import numpy as np
+    import synth
+    reqs = synth.request_stream(rate_hz=200.0, duration_s=args.serve_seconds, seed=5)
+    pools = {"plummer": synth.plummer(1 << 21, 51), "uniform": synth.uniform_cube(1 << 21, 52)}
+    payload = []
+    for r in reqs:
+        rng = np.random.default_rng(r.seed)
+        pm_pool, v_pool = pools[r.kind]
+        idx = rng.choice(len(pm_pool), r.n, replace=False)
+        pm = np.ascontiguousarray(pm_pool[idx])
+        pm[:, 3] = np.float32(1.0 / r.n)
+        payload.append((pm, np.ascontiguousarray(v_pool[idx])))
+    srv = B.bh_server_create(160 << 30, 256)
+    tickets = [None] * len(reqs)
+    try:
+        t0 = time.perf_counter()
+
+        def submit():
+            for k, (r, (pm, v)) in enumerate(zip(reqs, payload)):
+                delay = r.arrival_s - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[k] = B.bh_submit(srv, pm, v, 1.0, r.eps, r.theta, r.dt, r.steps)
+
+        th = threading.Thread(target=submit)
+        th.start()
+        th.join()
+        res = [B.bh_wait(srv, t, 0, 3600.0) for t in tickets]
+        stats = B.bh_server_stats_get(srv)
+    finally:
+        B.bh_server_destroy(srv)
+    lat = np.array([x["done_s"] - x["submit_s"] for x in res])
+    ps = sum(r.n * r.steps for r in reqs)
+    span = max(x["done_s"] for x in res) - min(x["submit_s"] for x in res)
+    offered = ps / max(args.serve_seconds, 1e-9)
+    return {"workload": f"{len(reqs)} requests, Poisson 200/s over {args.serve_seconds} s, "
+                        "N log-uniform [1024, 2097152], theta U[0.5,0.8], 10-200 steps dt 1e-3, "
+                        "Plummer/uniform 50/50, seed 5",
+            "value": ps / span, "unit": UNIT, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)),
+            "offered_particle_steps_per_s": offered, "requests": len(reqs),
+            "peak_resident_systems": stats["peak_resident_systems"],
+            "ticks": stats["ticks"], "busy_s": stats["busy_s"]}
 
 
 def main():
@@ -302,6 +413,14 @@ def main():
     ap.add_argument("--warps", type=int, default=8)
     ap.add_argument("--group", type=int, default=1, help="lanes voting together (1, 4, 8 or 32)")
     ap.add_argument("--no-kahan", action="store_true", help="plain FP32 force sums")
+    ap.add_argument("--no-graph", action="store_true", help="launch each step's kernels directly")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--forest-systems", type=int, default=512)
+    ap.add_argument("--forest-steps", type=int, default=100)
+    ap.add_argument("--plain-steps", type=int, default=10)
+    ap.add_argument("--serve-seconds", type=float, default=0.5,
+                    help="length of the Poisson arrival window (200 requests/s)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

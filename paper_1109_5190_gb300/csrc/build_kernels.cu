@@ -270,6 +270,7 @@ __device__ __forceinline__ int common_levels(uint64_t a, uint64_t b)
 // them is a leaf (one particle, or the level-21 bucket of equal keys).
 struct Span {
     int dprev, dnext, lmax, cnt;
+    int lo, hi;  // levels of the nodes the bottom-up pass computes (lo > hi: none)
 };
 
 __device__ __forceinline__ Span node_span(const uint64_t *__restrict__ key, int j, int a, int b)
@@ -281,9 +282,15 @@ __device__ __forceinline__ Span node_span(const uint64_t *__restrict__ key, int 
     if (s.dprev >= kLevels) {
         s.lmax = s.dprev;
         s.cnt = 0;
+        s.lo = 1;
+        s.hi = 0;
     } else {
         s.lmax = min(kLevels, max(s.dprev, s.dnext) + 1);
         s.cnt = s.lmax - s.dprev;
+        // the root is written by the topology pass, and so is the deepest node
+        // when it is a one-particle leaf (it is a bucket only if dnext = 21)
+        s.lo = max(s.dprev + 1, 1);
+        s.hi = s.lmax > s.dnext ? s.lmax - 1 : s.lmax;
     }
     return s;
 }
@@ -305,7 +312,7 @@ k_topo_count(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
         const int j = c.y + i;
         const Span s = node_span(key, j, S.start, S.start + S.n);
         ncount[j] = (uint32_t)s.cnt;
-        for (int l = s.dprev + 1; l <= s.lmax; ++l) atomicAdd(&h[l], 1u);
+        for (int l = s.lo; l <= s.hi; ++l) atomicAdd(&h[l], 1u);
     }
     __syncthreads();
     if (threadIdx.x < kNumLevels && h[threadIdx.x])
@@ -378,7 +385,7 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
         const int i = k * kChunkThreads + threadIdx.x;
         if (i >= c.z) break;
         const Span s = node_span(key, c.y + i, a, b);
-        for (int l = s.dprev + 1; l <= s.lmax; ++l) atomicAdd(&h[l], 1u);
+        for (int l = s.lo; l <= s.hi; ++l) atomicAdd(&h[l], 1u);
     }
     __syncthreads();
     if (threadIdx.x < kNumLevels) {
@@ -415,7 +422,13 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
             nodeR[n] = make_int4(j, count, l, 0);
             // low part 0 with scale 2^0 until the centre-of-mass pass fills it
             nodeW[n].b = make_uint4(__float_as_uint(crit), noff[end], 0u, 127u << 16);
-            nlist[base[l] + atomicAdd(&h[l], 1u)] = n;
+            if (l >= s.lo && l <= s.hi) {
+                nlist[base[l] + atomicAdd(&h[l], 1u)] = n;
+            } else if (l > 0) {  // one-particle leaf: the particle itself
+                const float4 p = spos[j];
+                nodeW[n].a = p;
+                nodeD[n] = make_double4(p.w, p.x, p.y, p.z);
+            }
             if (l == 0) {
                 if (count == 1) {
                     const float4 p = spos[j];
@@ -435,11 +448,12 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
 
 // ------------------------------------------------- centre of mass (A6)
 
-// Bottom-up, one launch per level (deepest first), in FP64: a one-particle
-// leaf takes its particle; a bucket sums its particles; an internal node sums
-// its children (first child = next node, then skip pointers):
+// Bottom-up, one launch per level (deepest first), in FP64, over the nodes
+// of that level that are not one-particle leaves (those, and the roots, are
+// written by the topology pass): a bucket sums its particles; an internal
+// node sums its children (first child = next node, then skip pointers):
 // M = sum m_c, com = sum m_c com_c / M.  The FP64 result is kept (nodeD) and
-// split into an FP32 high part and the FP32-rounded remainder for the walk.
+// split into an FP32 high part and a packed low part for the walk.
 __global__ void __launch_bounds__(256)
 k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
             WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4 *__restrict__ nodeD,
@@ -454,12 +468,6 @@ k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict_
         const uint4 B = nodeW[n].b;
         const float crit = wn_crit(B);
         const int skip = wn_skip(B);
-        if (crit == kLeafCrit) {
-            const float4 p = spos[C.x];
-            nodeW[n].a = p;
-            nodeD[n] = make_double4(p.w, p.x, p.y, p.z);
-            continue;
-        }
         double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
         if (crit == kBucketCrit) {
             for (int q = C.x; q < C.x + C.y; ++q) {
@@ -479,7 +487,8 @@ k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict_
                 sz += d.x * d.w;
             }
         }
-        const double cx = sx / M, cy = sy / M, cz = sz / M;
+        const double inv = 1.0 / M;
+        const double cx = sx * inv, cy = sy * inv, cz = sz * inv;
         const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
         nodeD[n] = make_double4(M, cx, cy, cz);
         nodeW[n].a = make_float4(hx, hy, hz, (float)M);

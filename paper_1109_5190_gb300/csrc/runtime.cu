@@ -195,26 +195,34 @@ struct Forest {
 
     bool acc_valid = false;
     bool tree_valid = false;
-    bh_tuning tune{1, 8, 0, 1};
+    bh_tuning tune{1, 8, 0, 2};
 
     cudaGraphExec_t gexec = nullptr;
     int g_nsteps = -1;
     unsigned g_cap = 0;
     bh_tuning g_tune{0, 0, 0, 0};
     int g_ntotal = -1;
+    bool g_prof = false;  // the graph carries phase events
 
     bool do_walk = true;
     int64_t last_step_launches = 0;
+    // phase profiling: events around the phases of each step, on st.  Steps
+    // enqueued directly use ev_plain (recycled after each run); steps captured
+    // in the graph use ev_graph (re-recorded by every replay).
     bool prof = false;
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
-    std::vector<std::array<int, 5>> prof_steps;
+    bool capturing = false;
+    std::vector<cudaEvent_t> ev_plain, ev_graph;
+    size_t ev_plain_used = 0;
+    std::vector<std::array<int, 5>> plain_marks, graph_marks;
+    double prof_ms[BH_NPHASE] = {0, 0, 0};
+    int64_t prof_nsteps = 0;
     int64_t launches = 0;
 
     ~Forest()
     {
         if (gexec) cudaGraphExecDestroy(gexec);
-        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_plain) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_graph) cudaEventDestroy(e);
         if (ev_sync) cudaEventDestroy(ev_sync);
         if (h_small) cudaFreeHost(h_small);
         if (st) cudaStreamDestroy(st);
@@ -451,13 +459,34 @@ struct Forest {
     int mark()
     {
         if (!prof) return -1;
-        if (ev_used == ev_pool.size()) {
+        std::vector<cudaEvent_t> &pool = capturing ? ev_graph : ev_plain;
+        const size_t idx = capturing ? ev_graph_next++ : ev_plain_used++;
+        while (pool.size() <= idx) {
             cudaEvent_t e;
             if (cudaEventCreate(&e) != cudaSuccess) return -1;
-            ev_pool.push_back(e);
+            pool.push_back(e);
         }
-        cudaEventRecord(ev_pool[ev_used], st);
-        return (int)ev_used++;
+        cudaEventRecord(pool[idx], st);
+        return (int)idx;
+    }
+
+    size_t ev_graph_next = 0;
+
+    // Adds the device time of the recorded steps' phases to prof_ms.
+    void accumulate(const std::vector<std::array<int, 5>> &marks, const std::vector<cudaEvent_t> &pool)
+    {
+        for (const auto &m : marks) {
+            if (m[0] < 0 || m[4] < 0) continue;
+            float a = 0, b2 = 0, c = 0, d = 0;
+            cudaEventElapsedTime(&a, pool[m[0]], pool[m[1]]);
+            cudaEventElapsedTime(&b2, pool[m[1]], pool[m[2]]);
+            cudaEventElapsedTime(&c, pool[m[2]], pool[m[3]]);
+            cudaEventElapsedTime(&d, pool[m[3]], pool[m[4]]);
+            prof_ms[0] += a + d;
+            prof_ms[1] += b2;
+            prof_ms[2] += c;
+            prof_nsteps += 1;
+        }
     }
 
     void reset_step_counters()
@@ -490,7 +519,7 @@ struct Forest {
         m[3] = mark();
         launch_kick(b, st);
         m[4] = mark();
-        if (prof) prof_steps.push_back(m);
+        if (prof) (capturing ? graph_marks : plain_marks).push_back(m);
         last_step_launches = g_launches;
         launches += g_launches;
         CKR(cudaGetLastError());
@@ -514,13 +543,15 @@ struct Forest {
     {
         invalidate_graph();
         cudaGraph_t g = nullptr;
-        const bool was_prof = prof;
-        prof = false;
+        graph_marks.clear();
+        ev_graph_next = 0;
+        capturing = true;
         CKR(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         int rc = BH_OK;
         for (int k = 0; k < nsteps && rc == BH_OK; ++k) rc = enqueue_step();
         cudaError_t e = cudaStreamEndCapture(st, &g);
-        prof = was_prof;
+        capturing = false;
+        g_prof = prof;
         if (rc != BH_OK) {
             if (g) cudaGraphDestroy(g);
             return rc;
@@ -551,7 +582,7 @@ struct Forest {
             if (graph) {
                 walk_max_blocks_per_sm(shape(), kahan(), pot());  // occupancy query outside capture
                 if (!gexec || g_nsteps != remaining || g_cap != node_cap || g_ntotal != n_total ||
-                    std::memcmp(&g_tune, &tune, sizeof tune) != 0)
+                    std::memcmp(&g_tune, &tune, sizeof tune) != 0 || (prof && !g_prof))
                     TRY(capture_graph(remaining));
                 CKR(cudaGraphLaunch(gexec, st));
                 launches += (int64_t)remaining * steps_launches();
@@ -559,6 +590,15 @@ struct Forest {
                 for (int k = 0; k < remaining; ++k) TRY(enqueue_step());
             }
             TRY(read_small());
+            if (prof) {
+                if (graph) {
+                    if (g_prof) accumulate(graph_marks, ev_graph);
+                } else {
+                    accumulate(plain_marks, ev_plain);
+                }
+                plain_marks.clear();
+                ev_plain_used = 0;
+            }
             const Small &h = *h_small;
             if (h.status == ST_OK) {
                 remaining = 0;
@@ -776,26 +816,27 @@ struct Forest {
         return BH_OK;
     }
 
+    void profile_begin()
+    {
+        prof = true;
+        plain_marks.clear();
+        ev_plain_used = 0;
+        for (int k = 0; k < BH_NPHASE; ++k) prof_ms[k] = 0;
+        prof_nsteps = 0;
+        launches = 0;
+        if (gexec && !g_prof) invalidate_graph();  // recapture with the events
+    }
+
     int profile_end(double *phase_ms, int64_t *steps, int64_t *nl)
     {
         TRY(sync());
-        double ph[BH_NPHASE] = {0, 0, 0};
-        for (auto &m : prof_steps) {
-            float a = 0, b2 = 0, c = 0, d = 0;
-            cudaEventElapsedTime(&a, ev_pool[m[0]], ev_pool[m[1]]);
-            cudaEventElapsedTime(&d, ev_pool[m[3]], ev_pool[m[4]]);
-            cudaEventElapsedTime(&b2, ev_pool[m[1]], ev_pool[m[2]]);
-            cudaEventElapsedTime(&c, ev_pool[m[2]], ev_pool[m[3]]);
-            ph[0] += a + d;
-            ph[1] += b2;
-            ph[2] += c;
-        }
-        if (phase_ms) for (int k = 0; k < BH_NPHASE; ++k) phase_ms[k] = ph[k];
-        if (steps) *steps = (int64_t)prof_steps.size();
+        accumulate(plain_marks, ev_plain);
+        plain_marks.clear();
+        ev_plain_used = 0;
+        if (phase_ms) for (int k = 0; k < BH_NPHASE; ++k) phase_ms[k] = prof_ms[k];
+        if (steps) *steps = prof_nsteps;
         if (nl) *nl = launches;
         prof = false;
-        prof_steps.clear();
-        ev_used = 0;
         return BH_OK;
     }
 };
@@ -1011,10 +1052,7 @@ int bh_autotune(bh_system *s, bh_tuning *best)
 int bh_profile_begin(bh_system *s)
 {
     if (!s) return fail(BH_ERR_INVALID, "null system");
-    s->f.prof = true;
-    s->f.prof_steps.clear();
-    s->f.ev_used = 0;
-    s->f.launches = 0;
+    s->f.profile_begin();
     return BH_OK;
 }
 

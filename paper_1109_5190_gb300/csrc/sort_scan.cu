@@ -217,13 +217,48 @@ k_scan_apply(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n,
     }
 }
 
+// One block scans up to kScanSingleMax values: rows of 4096 (4 per thread,
+// contiguous, so loads coalesce) with a running carry.
+constexpr int kScanSingleMax = 65536;
+
+__global__ void __launch_bounds__(1024)
+k_scan_single(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n,
+              uint32_t *__restrict__ total, const int *__restrict__ status)
+{
+    if (status && *status) return;
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < n; b0 += 1024 * 4) {
+        const int base = b0 + threadIdx.x * 4;
+        uint32_t x[4], s = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            x[q] = (base + q < n) ? in[base + q] : 0u;
+            s += x[q];
+        }
+        uint32_t tot;
+        uint32_t e = block_exclusive(s, &tot) + carry;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (base + q < n) out[base + q] = e;
+            e += x[q];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
 }  // namespace
 
 void launch_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *partials, uint32_t *total,
                  const int *status, cudaStream_t st)
 {
+    if (n <= 0) return;
+    if (n <= kScanSingleMax) {
+        k_scan_single<<<1, 1024, 0, st>>>(in, out, n, total, status);
+        g_launches += 1;
+        return;
+    }
     const int nb = (n + kScanTile - 1) / kScanTile;
-    if (nb == 0) return;
     k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, n, partials, status);
     k_scan_part<<<1, 1024, 0, st>>>(partials, nb, total, status);
     k_scan_apply<<<nb, kScanThreads, 0, st>>>(in, out, n, partials, status);

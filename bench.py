@@ -213,6 +213,8 @@ def run_gpu(args):
     ws1 = B.bh_walk_stats(h)
     inter1 = ws1["interactions"]
     dev_ms = float(phase_ms.sum())
+    if nsteps != args.steps or dev_ms <= 0:
+        raise RuntimeError(f"phase events recorded {nsteps} steps / {dev_ms} ms for {args.steps} steps")
 
     t_max = dev_ms
     if ws > 1:

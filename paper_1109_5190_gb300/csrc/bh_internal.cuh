@@ -170,6 +170,9 @@ struct BuildBufs {
     Small *small;
     int n_total;
     int nsm;
+    // levels deep_cut .. 21 hold few nodes: their centres of mass are done in
+    // one single-block launch (22 = none); any value gives the same result
+    int deep_cut;
 };
 
 void launch_kick_drift_bbox(const BuildBufs &b, cudaStream_t st);

@@ -448,12 +448,48 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
 
 // ------------------------------------------------- centre of mass (A6)
 
-// Bottom-up, one launch per level (deepest first), in FP64, over the nodes
-// of that level that are not one-particle leaves (those, and the roots, are
-// written by the topology pass): a bucket sums its particles; an internal
-// node sums its children (first child = next node, then skip pointers):
+// Bottom-up, level by level (deepest first), in FP64, over the nodes of each
+// level that are not one-particle leaves (those, and the roots, are written by
+// the topology pass): a bucket sums its particles; an internal node sums its
+// children (first child = next node, then skip pointers):
 // M = sum m_c, com = sum m_c com_c / M.  The FP64 result is kept (nodeD) and
 // split into an FP32 high part and a packed low part for the walk.
+__device__ __forceinline__ void com_node(unsigned n, const float4 *__restrict__ spos,
+                                         WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR,
+                                         double4 *__restrict__ nodeD)
+{
+    const int4 C = nodeR[n];  // first, count, level
+    const uint4 B = nodeW[n].b;
+    const float crit = wn_crit(B);
+    const int skip = wn_skip(B);
+    double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    if (crit == kBucketCrit) {
+        for (int q = C.x; q < C.x + C.y; ++q) {
+            const float4 p = spos[q];
+            const double m = p.w;
+            M += m;
+            sx += m * (double)p.x;
+            sy += m * (double)p.y;
+            sz += m * (double)p.z;
+        }
+    } else {
+        for (int ch = (int)n + 1; ch < skip; ch = wn_skip(nodeW[ch].b)) {
+            const double4 d = nodeD[ch];
+            M += d.x;
+            sx += d.x * d.y;
+            sy += d.x * d.z;
+            sz += d.x * d.w;
+        }
+    }
+    const double inv = 1.0 / M;
+    const double cx = sx * inv, cy = sy * inv, cz = sz * inv;
+    const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
+    nodeD[n] = make_double4(M, cx, cy, cz);
+    nodeW[n].a = make_float4(hx, hy, hz, (float)M);
+    nodeW[n].b = wn_pack(crit, skip, cx, cy, cz, hx, hy, hz);
+}
+
+// One level, all blocks.
 __global__ void __launch_bounds__(256)
 k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
             WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4 *__restrict__ nodeD,
@@ -462,37 +498,24 @@ k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict_
     if (halted(sm)) return;
     const unsigned cnt = sm->level_cnt[l];
     const unsigned off = sm->level_off[l];
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x) {
-        const unsigned n = nlist[off + k];
-        const int4 C = nodeR[n];  // first, count, level
-        const uint4 B = nodeW[n].b;
-        const float crit = wn_crit(B);
-        const int skip = wn_skip(B);
-        double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-        if (crit == kBucketCrit) {
-            for (int q = C.x; q < C.x + C.y; ++q) {
-                const float4 p = spos[q];
-                const double m = p.w;
-                M += m;
-                sx += m * (double)p.x;
-                sy += m * (double)p.y;
-                sz += m * (double)p.z;
-            }
-        } else {
-            for (int ch = (int)n + 1; ch < skip; ch = wn_skip(nodeW[ch].b)) {
-                const double4 d = nodeD[ch];
-                M += d.x;
-                sx += d.x * d.y;
-                sy += d.x * d.z;
-                sz += d.x * d.w;
-            }
-        }
-        const double inv = 1.0 / M;
-        const double cx = sx * inv, cy = sy * inv, cz = sz * inv;
-        const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
-        nodeD[n] = make_double4(M, cx, cy, cz);
-        nodeW[n].a = make_float4(hx, hy, hz, (float)M);
-        nodeW[n].b = wn_pack(crit, skip, cx, cy, cz, hx, hy, hz);
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x)
+        com_node(nlist[off + k], spos, nodeW, nodeR, nodeD);
+}
+
+// The deep levels l_hi .. l_lo, which hold few nodes, in one block: a block
+// barrier separates the levels, so one launch replaces many near-empty ones.
+__global__ void __launch_bounds__(1024)
+k_com_deep(int l_hi, int l_lo, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
+           WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4 *__restrict__ nodeD,
+           const Small *__restrict__ sm)
+{
+    if (halted(sm)) return;
+    for (int l = l_hi; l >= l_lo; --l) {
+        const unsigned cnt = sm->level_cnt[l];
+        const unsigned off = sm->level_off[l];
+        for (unsigned k = threadIdx.x; k < cnt; k += blockDim.x)
+            com_node(nlist[off + k], spos, nodeW, nodeR, nodeD);
+        __syncthreads();
     }
 }
 
@@ -701,8 +724,15 @@ void launch_topology(const BuildBufs &b, cudaStream_t st)
 
 void launch_com(const BuildBufs &b, cudaStream_t st)
 {
-    const int grid = b.nsm * 8;
-    for (int l = kLevels; l >= 1; --l) {
+    const int grid = b.nsm * 2;
+    int l = kLevels;
+    if (b.deep_cut <= kLevels) {
+        k_com_deep<<<1, 1024, 0, st>>>(kLevels, b.deep_cut, b.nlist, b.spos, b.nodeW, b.nodeR,
+                                       b.nodeD, b.small);
+        g_launches += 1;
+        l = b.deep_cut - 1;
+    }
+    for (; l >= 1; --l) {
         k_com_level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeW, b.nodeR, b.nodeD, b.small);
         g_launches += 1;
     }

@@ -204,6 +204,12 @@ struct Forest {
     int g_ntotal = -1;
     bool g_prof = false;  // the graph carries phase events
 
+    // first level of the fused deep centre-of-mass launch, chosen from the
+    // previous build's level sizes (22 = none yet)
+    int deep_cut = kNumLevels;
+    // off where the set of systems changes between steps (the server): the
+    // previous build then says little about the next one's level sizes
+    bool adaptive_deep = true;
     bool do_walk = true;
     int64_t last_step_launches = 0;
     // phase profiling: events around the phases of each step, on st.  Steps
@@ -287,6 +293,7 @@ struct Forest {
         b.small = small();
         b.n_total = n_total;
         b.nsm = nsm;
+        b.deep_cut = deep_cut;
         return b;
     }
 
@@ -466,7 +473,10 @@ struct Forest {
             if (cudaEventCreate(&e) != cudaSuccess) return -1;
             pool.push_back(e);
         }
-        cudaEventRecord(pool[idx], st);
+        // inside a capture only an external record becomes a graph node that
+        // re-records the event on every replay
+        if (capturing) cudaEventRecordWithFlags(pool[idx], st, cudaEventRecordExternal);
+        else cudaEventRecord(pool[idx], st);
         return (int)idx;
     }
 
@@ -590,6 +600,7 @@ struct Forest {
                 for (int k = 0; k < remaining; ++k) TRY(enqueue_step());
             }
             TRY(read_small());
+            choose_deep_cut();
             if (prof) {
                 if (graph) {
                     if (g_prof) accumulate(graph_marks, ev_graph);
@@ -620,6 +631,21 @@ struct Forest {
         }
         tree_valid = true;
         return BH_OK;
+    }
+
+    // Deep levels whose nodes sum to at most kDeepNodes go to one launch.
+    void choose_deep_cut()
+    {
+        constexpr unsigned kDeepNodes = 16384;
+        if (!adaptive_deep) return;
+        unsigned sum = 0;
+        int cut = kNumLevels;
+        for (int l = kLevels; l >= 1; --l) {
+            sum += h_small->level_cnt[l];
+            if (sum > kDeepNodes) break;
+            cut = l;
+        }
+        deep_cut = cut;
     }
 
     // kernels per step, as counted by the launchers when the step was enqueued
@@ -1382,6 +1408,7 @@ int bh_server_create(bh_server **out, size_t hbm_budget, int max_slots, void *st
     s->max_slots = max_slots;
     s->flags = flags;
     TRY(s->forest.init(stream, flags));
+    s->forest.adaptive_deep = false;
     s->t0 = Clock::now();
     bh_server *raw = s.get();
     try {

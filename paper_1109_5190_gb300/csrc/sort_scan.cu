@@ -217,8 +217,9 @@ k_scan_apply(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n,
     }
 }
 
-// One block scans up to kScanSingleMax values: rows of 4096 (4 per thread,
-// contiguous, so loads coalesce) with a running carry.
+// One block scans up to kScanSingleMax values: each thread owns a contiguous
+// segment of up to 64, so one block-wide exclusive scan of the segment sums
+// does it (one round of barriers).
 constexpr int kScanSingleMax = 65536;
 
 __global__ void __launch_bounds__(1024)
@@ -226,25 +227,19 @@ k_scan_single(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n
               uint32_t *__restrict__ total, const int *__restrict__ status)
 {
     if (status && *status) return;
-    uint32_t carry = 0;
-    for (int b0 = 0; b0 < n; b0 += 1024 * 4) {
-        const int base = b0 + threadIdx.x * 4;
-        uint32_t x[4], s = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            x[q] = (base + q < n) ? in[base + q] : 0u;
-            s += x[q];
-        }
-        uint32_t tot;
-        uint32_t e = block_exclusive(s, &tot) + carry;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (base + q < n) out[base + q] = e;
-            e += x[q];
-        }
-        carry += tot;
+    const int per = (n + 1023) / 1024;
+    const int b = threadIdx.x * per;
+    const int e = min(n, b + per);
+    uint32_t s = 0;
+    for (int i = b; i < e; ++i) s += in[i];
+    uint32_t tot;
+    uint32_t run = block_exclusive(s, &tot);
+    for (int i = b; i < e; ++i) {
+        const uint32_t x = in[i];
+        out[i] = run;
+        run += x;
     }
-    if (threadIdx.x == 0 && total) *total = carry;
+    if (threadIdx.x == 0 && total) *total = tot;
 }
 
 }  // namespace

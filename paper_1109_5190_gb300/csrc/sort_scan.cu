@@ -18,9 +18,12 @@ namespace bh {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int kWarps = kChunkThreads / 32;        // 8
-constexpr int kPerWarp = kChunk / kWarps;         // 512
-constexpr int kRounds = kPerWarp / 32;            // 16
+// Sort blocks: one chunk of kChunk keys per block of kSortThreads threads;
+// warp w ranks elements [w * kPerWarp, (w + 1) * kPerWarp) in kRounds rounds.
+constexpr int kSortThreads = 1024;
+constexpr int kWarps = kSortThreads / 32;         // 32
+constexpr int kPerWarp = kChunk / kWarps;         // 128
+constexpr int kRounds = kPerWarp / 32;            // 4
 
 __device__ __forceinline__ unsigned lanemask_lt()
 {
@@ -34,7 +37,7 @@ __device__ __forceinline__ unsigned count_index(const SysStatic &S, int chunk, i
     return (unsigned)(kRadixBins * S.chunk0 + digit * S.nchunk + (chunk - S.chunk0));
 }
 
-__global__ void __launch_bounds__(kChunkThreads)
+__global__ void __launch_bounds__(kSortThreads)
 k_rs_hist(const uint64_t *__restrict__ key, const int4 *__restrict__ chunks,
           const SysStatic *__restrict__ sys, uint32_t *__restrict__ counts, int shift,
           const Small *__restrict__ sm)
@@ -62,7 +65,7 @@ k_rs_hist(const uint64_t *__restrict__ key, const int4 *__restrict__ chunks,
     }
 }
 
-__global__ void __launch_bounds__(kChunkThreads)
+__global__ void __launch_bounds__(kSortThreads, 2)
 k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
              uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
              const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
@@ -217,29 +220,34 @@ k_scan_apply(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n,
     }
 }
 
-// One block scans up to kScanSingleMax values: each thread owns a contiguous
-// segment of up to 64, so one block-wide exclusive scan of the segment sums
-// does it (one round of barriers).
-constexpr int kScanSingleMax = 65536;
+// One block scans up to kScanSingleMax values: rows of 4096 (4 per thread,
+// contiguous, so loads coalesce) with a running carry.
+constexpr int kScanSingleMax = 8192;
 
 __global__ void __launch_bounds__(1024)
 k_scan_single(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n,
               uint32_t *__restrict__ total, const int *__restrict__ status)
 {
     if (status && *status) return;
-    const int per = (n + 1023) / 1024;
-    const int b = threadIdx.x * per;
-    const int e = min(n, b + per);
-    uint32_t s = 0;
-    for (int i = b; i < e; ++i) s += in[i];
-    uint32_t tot;
-    uint32_t run = block_exclusive(s, &tot);
-    for (int i = b; i < e; ++i) {
-        const uint32_t x = in[i];
-        out[i] = run;
-        run += x;
+    uint32_t carry = 0;
+    for (int b0 = 0; b0 < n; b0 += 1024 * 4) {
+        const int base = b0 + threadIdx.x * 4;
+        uint32_t x[4], s = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            x[q] = (base + q < n) ? in[base + q] : 0u;
+            s += x[q];
+        }
+        uint32_t tot;
+        uint32_t e = block_exclusive(s, &tot) + carry;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (base + q < n) out[base + q] = e;
+            e += x[q];
+        }
+        carry += tot;
     }
-    if (threadIdx.x == 0 && total) *total = tot;
+    if (threadIdx.x == 0 && total) *total = carry;
 }
 
 }  // namespace
@@ -267,11 +275,11 @@ void launch_sort(const BuildBufs &b, cudaStream_t st)
     const int ncounts = kRadixBins * b.nchunks;
     for (int pass = 0; pass < kRadixPasses; ++pass) {
         const int shift = pass * kRadixBits;
-        k_rs_hist<<<b.nchunks, kChunkThreads, 0, st>>>(kin, b.chunks, b.sys, b.rs_counts, shift,
-                                                       b.small);
+        k_rs_hist<<<b.nchunks, kSortThreads, 0, st>>>(kin, b.chunks, b.sys, b.rs_counts, shift,
+                                                      b.small);
         launch_scan(b.rs_counts, b.rs_counts, ncounts, b.scan_part, nullptr, &b.small->status, st);
-        k_rs_scatter<<<b.nchunks, kChunkThreads, 0, st>>>(kin, vin, kout, vout, b.chunks, b.sys,
-                                                          b.rs_counts, shift, b.small);
+        k_rs_scatter<<<b.nchunks, kSortThreads, 0, st>>>(kin, vin, kout, vout, b.chunks, b.sys,
+                                                         b.rs_counts, shift, b.small);
         g_launches += 2;
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;

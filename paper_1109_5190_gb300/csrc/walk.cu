@@ -40,6 +40,16 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
+// The whole 32-byte node record in one 256-bit read-only load.
+__device__ __forceinline__ void load_node(const WNode *p, float4 &A, uint4 &B)
+{
+    float b0, b1, b2, b3;
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(A.x), "=f"(A.y), "=f"(A.z), "=f"(A.w), "=f"(b0), "=f"(b1), "=f"(b2), "=f"(b3)
+        : "l"(p));
+    B = make_uint4(__float_as_uint(b0), __float_as_uint(b1), __float_as_uint(b2), __float_as_uint(b3));
+}
+
 template <bool KAHAN>
 __device__ __forceinline__ void acc_add(float &s, float &c, float x)
 {
@@ -167,9 +177,9 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) vis[k] += nxt[k] == cur;
             }
-            const WNode *np = a.nodeW + cur;
-            const float4 A = __ldg(&np->a);
-            const uint4 B = __ldg(&np->b);
+            float4 A;
+            uint4 B;
+            load_node(a.nodeW + cur, A, B);
             const int skip = wn_skip(B);
             if (skip <= cur) {  // corrupt skip pointer: report, never spin
                 atomicExch(&sm->status, ST_WALK_LIMIT);

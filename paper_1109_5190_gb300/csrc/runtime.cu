@@ -195,7 +195,7 @@ struct Forest {
 
     bool acc_valid = false;
     bool tree_valid = false;
-    bh_tuning tune{1, 8, 0, 2};
+    bh_tuning tune{1, 16, 0, 1};
 
     cudaGraphExec_t gexec = nullptr;
     int g_nsteps = -1;
@@ -700,7 +700,7 @@ struct Forest {
         TRY(ensure_tree());
         // (group, particles per lane) candidates x warps per block
         const int shapes[8][2] = {{1, 1}, {1, 2}, {2, 1}, {4, 1}, {8, 1}, {32, 1}, {32, 2}, {32, 4}};
-        const int warps[3] = {4, 8, 16};
+        const int warps[2] = {8, 16};
         cudaEvent_t e0, e1;
         CKR(cudaEventCreate(&e0));
         CKR(cudaEventCreate(&e1));

@@ -182,7 +182,7 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     if args.ppl:
-        B.bh_set_tuning(h, args.ppl, args.warps, 0, args.group)
+        B.bh_set_tuning(h, args.ppl, args.warps, 0, args.group, args.static_share)
         tuning = B.bh_get_tuning(h)
     else:
         tuning = B.bh_autotune(h)
@@ -267,7 +267,7 @@ def run_gpu(args):
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                    "walk_shape": {"ppl": tuning[0], "warps_per_block": tuning[1],
-                                  "group": tuning[3]}},
+                                  "group": tuning[3], "static_share": tuning[4]}},
         "phase_ms_per_step": {"integrate": phase_ms[0] / nsteps, "build": build_ms, "walk": walk_ms},
         "wall_ms_per_step": 1e3 * wall / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fma_peak, "unit": "TFLOP/s",
@@ -415,6 +415,7 @@ def main():
     ap.add_argument("--warps", type=int, default=8)
     ap.add_argument("--group", type=int, default=1, help="lanes voting together (1, 4, 8 or 32)")
     ap.add_argument("--no-kahan", action="store_true", help="plain FP32 force sums")
+    ap.add_argument("--static-share", type=int, default=75)
     ap.add_argument("--no-graph", action="store_true", help="launch each step's kernels directly")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")

@@ -113,6 +113,9 @@ typedef struct bh_tuning {
     int warps_per_block;
     int blocks_per_sm;
     int group;
+    int static_share;  /* percent (0..90) of the tiles split into one contiguous
+                          range per block (neighbouring walks share L1); the
+                          rest are handed out by an atomic queue */
 } bh_tuning;
 
 typedef struct bh_system bh_system;

@@ -52,7 +52,7 @@ assert NODE_DTYPE.itemsize == C.sizeof(bh_node) == 24
 
 class bh_tuning(C.Structure):
     _fields_ = [("ppl", C.c_int), ("warps_per_block", C.c_int), ("blocks_per_sm", C.c_int),
-                ("group", C.c_int)]
+                ("group", C.c_int), ("static_share", C.c_int)]
 
 
 class bh_system_desc(C.Structure):
@@ -261,21 +261,21 @@ def bh_walk_stats(h) -> dict:
     return {"interactions": a.value, "warp_iterations": b.value, "slot_visits": c.value}
 
 
-def bh_set_tuning(h, ppl=1, warps_per_block=8, blocks_per_sm=0, group=1):
-    t = bh_tuning(ppl, warps_per_block, blocks_per_sm, group)
+def bh_set_tuning(h, ppl=1, warps_per_block=16, blocks_per_sm=0, group=1, static_share=75):
+    t = bh_tuning(ppl, warps_per_block, blocks_per_sm, group, static_share)
     return _check(lib.bh_set_tuning(h, C.byref(t)))
 
 
 def bh_get_tuning(h) -> tuple:
     t = bh_tuning()
     _check(lib.bh_get_tuning(h, C.byref(t)))
-    return (t.ppl, t.warps_per_block, t.blocks_per_sm, t.group)
+    return (t.ppl, t.warps_per_block, t.blocks_per_sm, t.group, t.static_share)
 
 
 def bh_autotune(h) -> tuple:
     t = bh_tuning()
     _check(lib.bh_autotune(h, C.byref(t)))
-    return (t.ppl, t.warps_per_block, t.blocks_per_sm, t.group)
+    return (t.ppl, t.warps_per_block, t.blocks_per_sm, t.group, t.static_share)
 
 
 def bh_profile_begin(h):
@@ -333,15 +333,15 @@ def bh_forest_get_state(h, sys: int, pos_mass=None, vel=None, acc=None):
     return _check(lib.bh_forest_get_state(h, int(sys), *ptrs, flags))
 
 
-def bh_forest_set_tuning(h, ppl=1, warps_per_block=8, blocks_per_sm=0, group=1):
-    t = bh_tuning(ppl, warps_per_block, blocks_per_sm, group)
+def bh_forest_set_tuning(h, ppl=1, warps_per_block=16, blocks_per_sm=0, group=1, static_share=0):
+    t = bh_tuning(ppl, warps_per_block, blocks_per_sm, group, static_share)
     return _check(lib.bh_forest_set_tuning(h, C.byref(t)))
 
 
 def bh_forest_autotune(h) -> tuple:
     t = bh_tuning()
     _check(lib.bh_forest_autotune(h, C.byref(t)))
-    return (t.ppl, t.warps_per_block, t.blocks_per_sm, t.group)
+    return (t.ppl, t.warps_per_block, t.blocks_per_sm, t.group, t.static_share)
 
 
 def bh_forest_info(h):

@@ -206,6 +206,7 @@ struct WalkArgs {
     const int *mode;
     Small *small;
     uint32_t *counts;  // per-particle interaction counts (virtual order) or null
+    int static_share;  // percent of tiles split into per-block contiguous ranges
 };
 
 // ppl: particles per lane; group: lanes that vote together on the next node

@@ -195,12 +195,12 @@ struct Forest {
 
     bool acc_valid = false;
     bool tree_valid = false;
-    bh_tuning tune{1, 16, 0, 1};
+    bh_tuning tune{1, 16, 0, 1, 75};
 
     cudaGraphExec_t gexec = nullptr;
     int g_nsteps = -1;
     unsigned g_cap = 0;
-    bh_tuning g_tune{0, 0, 0, 0};
+    bh_tuning g_tune{0, 0, 0, 0, 0};
     int g_ntotal = -1;
     bool g_prof = false;  // the graph carries phase events
 
@@ -453,6 +453,7 @@ struct Forest {
         a.mode = d_mode.as<int>();
         a.small = small();
         a.counts = counts;
+        a.static_share = tune.static_share;
         return a;
     }
 
@@ -706,30 +707,36 @@ struct Forest {
         CKR(cudaEventCreate(&e1));
         float best_ms = 1e30f;
         bh_tuning pick = tune;
+        const int shares[2] = {0, 75};
+        const bh_tuning saved = tune;
         for (const auto &gp : shapes) {
             const int g = gp[0], p = gp[1];
             TRY(ensure_tiles(p));
             for (int w : warps) {
-                bh_tuning t{p, w, 0, g};
-                WalkShape sh{p, w, 0, g};
-                if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0) continue;
-                float ms_best = 1e30f;
-                for (int rep = 0; rep < 3; ++rep) {
-                    reset_step_counters();
-                    cudaEventRecord(e0, st);
-                    launch_walk(walk_args(p, nullptr), sh, kahan(), pot(), false, nsm, st);
-                    cudaEventRecord(e1, st);
-                    CKR(cudaEventSynchronize(e1));
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep > 0 && ms < ms_best) ms_best = ms;
-                }
-                if (ms_best < best_ms) {
-                    best_ms = ms_best;
-                    pick = t;
+                for (int share : shares) {
+                    bh_tuning t{p, w, 0, g, share};
+                    WalkShape sh{p, w, 0, g};
+                    if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0) continue;
+                    tune = t;  // walk_args reads the static share from tune
+                    float ms_best = 1e30f;
+                    for (int rep = 0; rep < 3; ++rep) {
+                        reset_step_counters();
+                        cudaEventRecord(e0, st);
+                        launch_walk(walk_args(p, nullptr), sh, kahan(), pot(), false, nsm, st);
+                        cudaEventRecord(e1, st);
+                        CKR(cudaEventSynchronize(e1));
+                        float ms = 0;
+                        cudaEventElapsedTime(&ms, e0, e1);
+                        if (rep > 0 && ms < ms_best) ms_best = ms;
+                    }
+                    if (ms_best < best_ms) {
+                        best_ms = ms_best;
+                        pick = t;
+                    }
                 }
             }
         }
+        tune = saved;
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         CKR(cudaGetLastError());
@@ -748,6 +755,7 @@ struct Forest {
             t->warps_per_block > 32 || t->blocks_per_sm < 0 ||
             t->warps_per_block > 16 ||
             (t->group != 1 && t->group != 2 && t->group != 4 && t->group != 8 && t->group != 32) ||
+            t->static_share < 0 || t->static_share > 90 ||
             (t->group != 32 && t->ppl == 4) || (t->group == 2 && t->ppl != 1))
             return fail(BH_ERR_INVALID, "bad tuning (group 1/4/8 with ppl 1/2, group 2 with ppl 1, "
                                         "group 32 with ppl 1/2/4; warps 1..16; blocks_per_sm >= 0)");
@@ -1105,6 +1113,7 @@ int bh_forest_create(bh_forest **out, int nsys, const bh_system_desc *d, void *s
     if (!F) return fail(BH_ERR_OOM, "host allocation failed");
     Forest &f = F->f;
     TRY(f.init(stream, flags & (BH_POTENTIAL | BH_NO_KAHAN)));
+    f.tune.static_share = nsys > 1 ? 0 : f.tune.static_share;  // uneven tiles: all dynamic
     TRY(f.begin_call());
     for (int s = 0; s < nsys; ++s) {
         auto st = std::make_unique<SysState>();
@@ -1409,6 +1418,7 @@ int bh_server_create(bh_server **out, size_t hbm_budget, int max_slots, void *st
     s->flags = flags;
     TRY(s->forest.init(stream, flags));
     s->forest.adaptive_deep = false;
+    s->forest.tune.static_share = 0;  // requests differ widely in cost per tile
     s->t0 = Clock::now();
     bh_server *raw = s.get();
     try {

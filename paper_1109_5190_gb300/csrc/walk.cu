@@ -10,9 +10,9 @@
 // GPU design (sm_103a, FP32 ALU-bound; no tensor cores: this is not a dense
 // contraction):
 //   * Persistent kernel; each warp pulls tiles of 32*PPL consecutive
-//     Morton-sorted particles: first from its block's contiguous share of
-//     three quarters of the tiles (neighbouring walks share L1), then from an
-//     atomic queue over the rest (dynamic load balancing in place of the
+//     Morton-sorted particles: first from its block's contiguous share of a
+//     tunable fraction of the tiles (neighbouring walks share L1), then from
+//     an atomic queue over the rest (dynamic load balancing in place of the
 //     paper's runtime work queues, Section III).
 //   * Warp-cooperative traversal: nodes are stored in depth-first pre-order
 //     with a skip pointer (the first node after the subtree).  Each particle
@@ -122,14 +122,15 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
     const int lane = threadIdx.x & 31;
     Small *sm = a.small;
     if (sm->status) return;
-    // Tiles [0, nstatic) are split into one contiguous range per block, taken
-    // through a shared counter, so the warps of an SM walk neighbouring
-    // regions and share tree nodes in L1; the rest go through the global
-    // atomic queue, which evens out the blocks' finishing times.
+    // Tiles [0, nstatic) (static_share percent) are split into one contiguous
+    // range per block, taken through a shared counter, so the warps of an SM
+    // walk neighbouring regions and share tree nodes in L1; the rest go
+    // through the global atomic queue, which evens out the blocks' finishing
+    // times (all of them, when tile costs vary widely, as in a forest).
     __shared__ unsigned s_next;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
-    const int per_block = (int)(((long long)a.ntiles * 3 / 4) / gridDim.x);
+    const int per_block = (int)(((long long)a.ntiles * a.static_share / 100) / gridDim.x);
     const int nstatic = per_block * (int)gridDim.x;
     for (;;) {
         int t = 0;

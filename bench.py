@@ -109,6 +109,48 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def combine_ranks(local_ms: float, units_per_rank: int, steps: int, device=None):
+    """(slowest rank's time in ms, whole-job units/s): every rank ran `steps`
+    steps of `units_per_rank` units; max over ranks, no data-path collective
+    beyond this one scalar."""
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    t_max = float(local_ms)
+    if ws > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_max], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    return t_max, ws * units_per_rank * steps / (t_max * 1e-3)
+
+
+def walk_sources_sha() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("walk.cu", "bh_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1109_5190_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def walk_traffic():
+    """DRAM bytes per walk launch from the committed ncu capture summary, or
+    None once the walk's sources differ from the ones that capture measured."""
+    path = os.path.join(ROOT, "profiles", "walk_uniform1M_ncu.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    fields = dict(line.split(":", 1) for line in text.splitlines()
+                  if line.startswith(("walk_source_sha256:", "dram_bytes_per_launch:")))
+    if fields.get("walk_source_sha256", "").strip() != walk_sources_sha():
+        return None
+    try:
+        return int(fields["dram_bytes_per_launch"].strip())
+    except (KeyError, ValueError):
+        return None
+
+
 # ---------------------------------------------------------------- reference
 
 def cpu_sample(pm, sample: int, seed: int = 7):
@@ -216,12 +258,7 @@ def run_gpu(args):
     if nsteps != args.steps or dev_ms <= 0:
         raise RuntimeError(f"phase events recorded {nsteps} steps / {dev_ms} ms for {args.steps} steps")
 
-    t_max = dev_ms
-    if ws > 1:
-        tt = torch.tensor([dev_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = ws * N_PART * args.steps / (t_max * 1e-3)
+    t_max, value = combine_ranks(dev_ms, N_PART, args.steps, dev)
 
     # ---- roofline of the dominant kernel (the walk): FP32 ALU bound
     walk_ms = phase_ms[2] / nsteps
@@ -271,7 +308,7 @@ def run_gpu(args):
         "phase_ms_per_step": {"integrate": phase_ms[0] / nsteps, "build": build_ms, "walk": walk_ms},
         "wall_ms_per_step": 1e3 * wall / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fma_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fma_peak, "traffic": None,
+                     "frac": achieved / fma_peak, "traffic": walk_traffic(),
                      "kernel": "k_walk", "peak_source": "project FP32 FMA micro-benchmark",
                      "interactions_per_launch": inter, "flops_per_interaction": FLOPS_PER_INTERACTION,
                      "warp_iterations_per_launch": ws1["warp_iterations"],

@@ -295,6 +295,8 @@ def run_gpu(args):
         extra["batched"] = bench_batched(args, B, torch)
     if rank == 0 and not args.no_served:
         extra["served"] = bench_served(args, B, torch)
+    if rank == 0 and not args.no_large:
+        extra["large"] = bench_large(args, B, torch, fma_peak, peaks["hbm_gbs"])
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -385,6 +387,51 @@ def bench_batched(args, B, torch):
             "speedup_vs_plain": batched / plain}
 
 
+def bench_large(args, B, torch, fma_peak_tflops, hbm_gbs):
+    """Large single Plummer sphere: N = 16,777,216, masses 1/N, eps 0.002,
+    theta 0.6, 10 KDK steps dt 2.5e-4 (FP32 positions/velocities/forces, Kahan
+    force sums).  Build GB/s and walk interactions/s against their rooflines."""
+    import synth
+    n, theta, eps, dt, steps = 1 << 24, 0.6, 0.002, 2.5e-4, 10
+    pm, vel = synth.plummer(n, 3)
+    d_pm = torch.from_numpy(pm).cuda()
+    d_vel = torch.from_numpy(vel).cuda()
+    del pm, vel
+    h = B.bh_create(B.params(1.0, eps, theta), d_pm, d_vel, torch.cuda.current_stream())
+    del d_pm, d_vel
+    try:
+        shape = B.bh_autotune(h)
+        B.bh_compute_accel(h)
+        B.bh_profile_begin(h)
+        B.bh_step(h, 1, dt, True)  # capture + warm-up
+        B.bh_profile_end(h)
+        stats = B.bh_walk_stats(h)
+        nodes = B.bh_node_count(h)
+        torch.cuda.synchronize()
+        B.bh_profile_begin(h)
+        for _ in range(steps):
+            B.bh_step(h, 1, dt, True)
+        phase_ms, nst, _ = B.bh_profile_end(h)
+    finally:
+        B.bh_destroy(h)
+    walk_ms = phase_ms[2] / nst
+    build_ms = phase_ms[1] / nst
+    step_ms = float(phase_ms.sum()) / nst
+    inter_s = stats["interactions"] / (walk_ms * 1e-3)
+    build_gbs = (144 * n + 48 * nodes) / (build_ms * 1e-3) / 1e9
+    return {"workload": "Plummer N=16,777,216, m=1/N, eps=0.002, theta=0.6, 10 KDK steps dt=2.5e-4, seed 3",
+            "value": n / (step_ms * 1e-3), "unit": UNIT, "ms_per_step": step_ms,
+            "phase_ms_per_step": {"integrate": phase_ms[0] / nst, "build": build_ms, "walk": walk_ms},
+            "walk_shape": list(shape), "nodes": nodes,
+            "walk_interactions_per_s": inter_s,
+            "interactions_per_particle": stats["interactions"] / n,
+            "walk_roofline": {"bound": "alu", "achieved": inter_s * FLOPS_PER_INTERACTION / 1e12,
+                              "peak": fma_peak_tflops, "unit": "TFLOP/s",
+                              "frac": inter_s * FLOPS_PER_INTERACTION / 1e12 / fma_peak_tflops},
+            "build_roofline": {"bound": "hbm", "achieved": build_gbs, "peak": hbm_gbs, "unit": "GB/s",
+                               "frac": build_gbs / hbm_gbs}}
+
+
 def bench_served(args, B, torch):
     """Poisson request stream (200 requests/s; each request a Plummer or
     uniform system of N log-uniform in [1024, 2097152], theta U[0.5, 0.8],
@@ -456,6 +503,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="launch each step's kernels directly")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--forest-systems", type=int, default=512)
     ap.add_argument("--forest-steps", type=int, default=100)
     ap.add_argument("--plain-steps", type=int, default=10)

@@ -362,3 +362,31 @@ def test_uniform_cube_million_step0_all_particles():
             assert_accel_close(a[idx], ref, what=f"C2 step 2 theta={theta}")
         finally:
             B.bh_destroy(h)
+
+
+@pytest.mark.slow
+def test_large_plummer_sampled():
+    # configs[2]: Plummer N = 2^24, eps 0.002, theta 0.6, dt 2.5e-4: a seeded
+    # 4096-particle sample against the FP64 oracle (full oracle tree of all
+    # particles) at step 0 and after one KDK step.
+    n = 1 << 24
+    pm, vel = synth.plummer(n, 3)
+    d_pm = torch.from_numpy(pm).cuda()
+    d_vel = torch.from_numpy(vel).cuda()
+    h = B.bh_create(B.params(1.0, 0.002, 0.6), d_pm, d_vel)
+    del d_pm, d_vel
+    try:
+        idx = np.random.default_rng(21).choice(n, 4096, replace=False)
+        acc = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
+        B.bh_compute_accel(h, acc)
+        a = acc[torch.from_numpy(idx).cuda()].cpu().numpy()
+        ref, _, cnt = oracle.Tree(pm).accel(0.6, 0.002, targets=idx)
+        assert_accel_close(a, ref, what="C3 step 0")
+        B.bh_step(h, 1, 2.5e-4)
+        x = torch.zeros_like(acc)
+        B.bh_get_state(h, x, None, acc)
+        xs = x.cpu().numpy()
+        ref, _, _ = oracle.Tree(xs).accel(0.6, 0.002, targets=idx)
+        assert_accel_close(acc[torch.from_numpy(idx).cuda()].cpu().numpy(), ref, what="C3 step 1")
+    finally:
+        B.bh_destroy(h)

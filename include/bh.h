@@ -98,9 +98,10 @@ typedef struct bh_node {
 } bh_node;
 
 /* Walk launch shape (the autotuner's search space).
- *   ppl             particles per lane (1, 2 or 4; 4 only with group 32): a
- *                   warp task is a tile of 32*ppl consecutive Morton-sorted
- *                   particles
+ *   ppl             particles per lane (1, 2 or 4; 4 only with group 1 or 32):
+ *                   a warp task is a tile of 32*ppl consecutive Morton-sorted
+ *                   particles; with group < 32 a lane's particles are
+ *                   neighbours in that order
  *   warps_per_block 1..16
  *   blocks_per_sm   0 = as many as fit
  *   group           lanes that vote together on the next node (1, 2, 4, 8 or

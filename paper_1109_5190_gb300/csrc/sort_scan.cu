@@ -8,7 +8,8 @@
 // nothing extra: the per-(chunk, digit) counts are laid out system by system
 // as [system][digit][chunk], so one global exclusive scan yields offsets that
 // already include every earlier system's particles (chunks never straddle
-// systems).  Within a block, ranks come from warp-level __match_any_sync
+// systems).  Only the first pass has a histogram kernel: each scatter also
+// counts the next pass's digits per destination chunk.  Within a block, ranks come from warp-level __match_any_sync
 // groups: one leader per digit and round updates the warp's running count,
 // so no shared-memory atomics are needed and the order is stable.
 #include "bh.h"
@@ -69,7 +70,8 @@ __global__ void __launch_bounds__(kSortThreads, 2)
 k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
              uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
              const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
-             const uint32_t *__restrict__ offs, int shift, const Small *__restrict__ sm)
+             const uint32_t *__restrict__ offs, int shift, uint32_t *__restrict__ next_counts,
+             const Small *__restrict__ sm)
 {
     if (sm->status) return;
     __shared__ uint32_t h[kWarps][kRadixBins];
@@ -114,10 +116,24 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const unsigned d = rd[r] & 511u;
-        if (d < (unsigned)kRadixBins) {
-            const uint32_t dst = gbase[d] + h[w][d] + (rd[r] >> 9);
+        const bool valid = d < (unsigned)kRadixBins;
+        uint32_t dst = 0;
+        if (valid) {
+            dst = gbase[d] + h[w][d] + (rd[r] >> 9);
             kout[dst] = k[r];
             vout[dst] = v[r];
+        }
+        if (next_counts) {
+            // the next pass's histogram: count this key's next digit in the
+            // chunk it lands in (warp-aggregated global atomics)
+            unsigned idx = 0xffffffffu;
+            if (valid) {
+                const int chunk = S.chunk0 + ((int)dst - S.start) / kChunk;
+                const int nd = (int)((k[r] >> (shift + kRadixBits)) & (kRadixBins - 1));
+                idx = count_index(S, chunk, nd);
+            }
+            const unsigned peers = __match_any_sync(FULL, idx);
+            if (valid && (peers & lt) == 0) atomicAdd(&next_counts[idx], (unsigned)__popc(peers));
         }
     }
 }
@@ -273,16 +289,22 @@ void launch_sort(const BuildBufs &b, cudaStream_t st)
     uint64_t *kin = b.key0, *kout = b.key1;
     uint32_t *vin = b.val0, *vout = b.val1;
     const int ncounts = kRadixBins * b.nchunks;
+    // two count buffers: pass p scans and reads one while its scatter counts
+    // the next pass's digits into the other (zeroed just before)
+    uint32_t *cur = b.rs_counts, *nxt = b.rs_counts + ncounts;
+    k_rs_hist<<<b.nchunks, kSortThreads, 0, st>>>(kin, b.chunks, b.sys, cur, 0, b.small);
+    g_launches += 1;
     for (int pass = 0; pass < kRadixPasses; ++pass) {
         const int shift = pass * kRadixBits;
-        k_rs_hist<<<b.nchunks, kSortThreads, 0, st>>>(kin, b.chunks, b.sys, b.rs_counts, shift,
-                                                      b.small);
-        launch_scan(b.rs_counts, b.rs_counts, ncounts, b.scan_part, nullptr, &b.small->status, st);
-        k_rs_scatter<<<b.nchunks, kSortThreads, 0, st>>>(kin, vin, kout, vout, b.chunks, b.sys,
-                                                         b.rs_counts, shift, b.small);
-        g_launches += 2;
+        const bool more = pass + 1 < kRadixPasses;
+        launch_scan(cur, cur, ncounts, b.scan_part, nullptr, &b.small->status, st);
+        if (more) cudaMemsetAsync(nxt, 0, sizeof(uint32_t) * (size_t)ncounts, st);
+        k_rs_scatter<<<b.nchunks, kSortThreads, 0, st>>>(kin, vin, kout, vout, b.chunks, b.sys, cur,
+                                                         shift, more ? nxt : nullptr, b.small);
+        g_launches += 1;
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
+        uint32_t *tc = cur; cur = nxt; nxt = tc;
     }
 }
 

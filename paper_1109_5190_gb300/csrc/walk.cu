@@ -83,6 +83,17 @@ __device__ __noinline__ bool accept_fp64(const double4 *__restrict__ nodeD,
     return __dmul_rn(s, s) < __dmul_rn(theta2, d2);
 }
 
+// Offset within its tile of a lane's k-th particle.  When the whole warp
+// votes (GROUP 32) every lane sees the union anyway, so slot k of all lanes is
+// one contiguous run of 32; with smaller vote groups a lane's own particles
+// are neighbours in Morton order, so their traversals nearly coincide and one
+// node load serves all of them.
+template <int PPL, int GROUP>
+__device__ __forceinline__ int slot_offset(int lane, int k)
+{
+    return GROUP == 32 ? k * 32 + lane : lane * PPL + k;
+}
+
 // One softened monopole term added to a particle slot's sums.
 template <bool KAHAN, bool POT, bool COUNT>
 __device__ __forceinline__ void interact(float m, float dx, float dy, float dz, float d2, float eps2,
@@ -157,7 +168,7 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
         unsigned iters = 0;
 #pragma unroll
         for (int k = 0; k < PPL; ++k) {
-            const int o = k * 32 + lane;
+            const int o = slot_offset<PPL, GROUP>(lane, k);
             myj[k] = tl.start + o;
             ax[k] = ay[k] = az[k] = cx[k] = cy[k] = cz[k] = pp[k] = cp[k] = 0.f;
             cnt[k] = vis[k] = 0;
@@ -256,8 +267,9 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
             unsigned long long ci = 0, cv = 0, it = iters;
 #pragma unroll
             for (int k = 0; k < PPL; ++k) {
-                ci += (k * 32 + lane < tl.count) ? cnt[k] : 0u;
-                cv += (k * 32 + lane < tl.count) ? vis[k] : 0u;
+                const bool live = slot_offset<PPL, GROUP>(lane, k) < tl.count;
+                ci += live ? cnt[k] : 0u;
+                cv += live ? vis[k] : 0u;
             }
             for (int o = 16; o > 0; o >>= 1) {
                 ci += __shfl_down_sync(FULL, ci, o);
@@ -274,7 +286,7 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
         float4 *acc = S.acc;
 #pragma unroll
         for (int k = 0; k < PPL; ++k) {
-            const int o = k * 32 + lane;
+            const int o = slot_offset<PPL, GROUP>(lane, k);
             if (o < tl.count) {
                 const uint32_t v = a.sid[myj[k]];
                 if (COUNT) a.counts[v] = cnt[k];
@@ -361,6 +373,7 @@ struct Variants {
         switch (key) {
             case 1 * 8 + 1: return pick<1, 1>(kahan, pot, a, sh, nsm, st);
             case 1 * 8 + 2: return pick<2, 1>(kahan, pot, a, sh, nsm, st);
+            case 1 * 8 + 4: return pick<4, 1>(kahan, pot, a, sh, nsm, st);
             case 2 * 8 + 1: return pick<1, 2>(kahan, pot, a, sh, nsm, st);
             case 4 * 8 + 1: return pick<1, 4>(kahan, pot, a, sh, nsm, st);
             case 4 * 8 + 2: return pick<2, 4>(kahan, pot, a, sh, nsm, st);

@@ -219,7 +219,8 @@ def test_launch_shape_does_not_change_results():
     h = make(pm, eps=0.005, theta=0.6)
     try:
         ref = None
-        for group, ppl in ((1, 1), (1, 2), (4, 1), (4, 2), (8, 1), (8, 2), (32, 1), (32, 2), (32, 4)):
+        for group, ppl in ((1, 1), (1, 2), (1, 4), (2, 1), (4, 1), (4, 2), (8, 1), (8, 2), (32, 1),
+                           (32, 2), (32, 4)):
             for w in (4, 8, 16):
                 B.bh_set_tuning(h, ppl, w, 0, group)
                 a = gpu_accel(h, 20000)
@@ -229,7 +230,7 @@ def test_launch_shape_does_not_change_results():
                 st = B.bh_walk_stats(h)
                 assert st["interactions"] <= 32 * st["warp_iterations"] * ppl
         with pytest.raises(B.BHError):
-            B.bh_set_tuning(h, 4, 8, 0, 1)  # four particles per lane only with the warp vote
+            B.bh_set_tuning(h, 4, 8, 0, 4)  # four particles per lane: lone lanes or the warp vote
         best = B.bh_autotune(h)
         assert best[0] in (1, 2, 4) and best[3] in (1, 32)
         assert np.array_equal(gpu_accel(h, 20000), ref)

@@ -233,15 +233,20 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
                     if (kSolo || nxt[k] == cur) nxt[k] = skip;
             } else {
                 const float band = crit * kTieBand;  // negative for leaves: never a tie
-                float lx, ly, lz;
-                wn_lo(B, lx, ly, lz);
+                // low part of the centre of mass: int16 multiples of a power of two,
+                // folded into the distance by one fused multiply-add per axis
+                // (the product is exact, so this equals adding the decoded value)
+                const float lscale = __int_as_float((int)(B.w >> 16) << 23);
+                const float lqx = (float)(short)(B.z & 0xffffu);
+                const float lqy = (float)(short)(B.z >> 16);
+                const float lqz = (float)(short)(B.w & 0xffffu);
 #pragma unroll
                 for (int k = 0; k < PPL; ++k) {
                     if (kSolo || nxt[k] == cur) {
                         // distance to the centre of mass from its high and low parts
-                        const float dx = (A.x - px[k]) + lx;
-                        const float dy = (A.y - py[k]) + ly;
-                        const float dz = (A.z - pz[k]) + lz;
+                        const float dx = fmaf(lqx, lscale, A.x - px[k]);
+                        const float dy = fmaf(lqy, lscale, A.y - py[k]);
+                        const float dz = fmaf(lqz, lscale, A.z - pz[k]);
                         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
                         const float diff = d2 - crit;
                         bool acc = diff > 0.f;

@@ -207,6 +207,7 @@ struct WalkArgs {
     Small *small;
     uint32_t *counts;  // per-particle interaction counts (virtual order) or null
     int static_share;  // percent of tiles split into per-block contiguous ranges
+    int nsm;           // SMs the persistent grid is spread over
 };
 
 // ppl: particles per lane; group: lanes that vote together on the next node

@@ -454,6 +454,7 @@ struct Forest {
         a.small = small();
         a.counts = counts;
         a.static_share = tune.static_share;
+        a.nsm = nsm;
         return a;
     }
 

@@ -94,6 +94,18 @@ __device__ __forceinline__ int slot_offset(int lane, int k)
     return GROUP == 32 ? k * 32 + lane : lane * PPL + k;
 }
 
+// Static range of this block.  Persistent blocks are dealt to SMs round
+// robin (block b on SM b mod #SMs), so ranges are numbered SM by SM: the
+// blocks that share an SM take neighbouring ranges and their walks share L1.
+// Any other placement is still correct, only with less sharing.
+__device__ __forceinline__ int range_of_block(int nsm)
+{
+    const int bps = nsm > 0 ? (int)gridDim.x / nsm : 1;  // the grid is nsm * bps blocks
+    const int b = (int)blockIdx.x;
+    if (bps <= 1 || bps * nsm != (int)gridDim.x) return b;
+    return (b % nsm) * bps + b / nsm;
+}
+
 // One softened monopole term added to a particle slot's sums.
 template <bool KAHAN, bool POT, bool COUNT>
 __device__ __forceinline__ void interact(float m, float dx, float dy, float dz, float d2, float eps2,
@@ -147,7 +159,7 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
         int t = 0;
         if (lane == 0) {
             const int k = (int)atomicAdd(&s_next, 1u);
-            t = k < per_block ? (int)blockIdx.x * per_block + k
+            t = k < per_block ? range_of_block(a.nsm) * per_block + k
                               : nstatic + (int)atomicAdd(&sm->queue, 1u);
         }
         t = __shfl_sync(FULL, t, 0);

@@ -35,6 +35,23 @@ WORKLOAD = ("uniform cube N=1,048,576 U[-1,1]^3, v=0, m=1/N, G=1, eps=0.005, the
             "dt=5e-4 KDK leapfrog, FP32 walk (Kahan) + FP64 root reductions, seed 2")
 N_PART = 1 << 20
 THETA, EPS, DT, SEED = 0.5, 0.005, 5e-4, 2
+KIND = "uniform"
+WORKLOADS = {
+    # the headline workload (default)
+    "uniform1m": dict(N_PART=1 << 20, THETA=0.5, EPS=0.005, DT=5e-4, SEED=2, KIND="uniform",
+                      WORKLOAD=WORKLOAD),
+    # the large single Plummer sphere, selectable as the main leg (for profiling)
+    "large": dict(N_PART=1 << 24, THETA=0.6, EPS=0.002, DT=2.5e-4, SEED=3, KIND="plummer",
+                  WORKLOAD="Plummer N=16,777,216, m=1/N, G=1, eps=0.002, theta=0.6, "
+                           "dt=2.5e-4 KDK leapfrog, FP32 walk (Kahan) + FP64 root reductions, seed 3"),
+}
+
+
+def make_inputs():
+    import synth
+    if KIND == "plummer":
+        return synth.plummer(N_PART, SEED)
+    return synth.uniform_cube(N_PART, SEED)
 FLOPS_PER_INTERACTION = 20
 
 
@@ -176,7 +193,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import synth
-    pm, _ = synth.uniform_cube(N_PART, SEED)
+    pm, _ = make_inputs()
     sample = args.ref_sample
     vals, spent = [], 0.0
     for k in range(args.warmup + args.steps):
@@ -216,7 +233,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
 
-    pm, vel = synth.uniform_cube(N_PART, SEED)
+    pm, vel = make_inputs()
     d_pm = torch.from_numpy(pm).to(dev)
     d_vel = torch.from_numpy(vel).to(dev)
     flags = B.BH_NO_KAHAN if args.no_kahan else 0
@@ -509,7 +526,9 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--serve-seconds", type=float, default=0.5,
                     help="length of the Poisson arrival window (200 requests/s)")
+    ap.add_argument("--workload", default="uniform1m", choices=sorted(WORKLOADS))
     args = ap.parse_args()
+    globals().update(WORKLOADS[args.workload])
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
     if args.impl == "reference":

@@ -178,6 +178,7 @@ struct BuildBufs {
 void launch_kick_drift_bbox(const BuildBufs &b, cudaStream_t st);
 void launch_keys(const BuildBufs &b, cudaStream_t st);
 void launch_sort(const BuildBufs &b, cudaStream_t st);
+void prepare_sort_kernels();
 void launch_permute(const BuildBufs &b, cudaStream_t st);
 void launch_topology(const BuildBufs &b, cudaStream_t st);
 void launch_com(const BuildBufs &b, cudaStream_t st);

@@ -241,6 +241,7 @@ struct Forest {
         CKR(cudaGetDevice(&dev));
         CKR(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         CKR(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+        prepare_sort_kernels();
         CKR(cudaEventCreateWithFlags(&ev_sync, cudaEventDisableTiming));
         CKR(cudaMallocHost(&h_small, sizeof(Small)));
         std::memset(h_small, 0, sizeof(Small));

@@ -66,80 +66,6 @@ k_rs_hist(const uint64_t *__restrict__ key, const int4 *__restrict__ chunks,
     }
 }
 
-__global__ void __launch_bounds__(kSortThreads, 2)
-k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
-             uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
-             const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
-             const uint32_t *__restrict__ offs, int shift, uint32_t *__restrict__ next_counts,
-             const Small *__restrict__ sm)
-{
-    if (sm->status) return;
-    __shared__ uint32_t h[kWarps][kRadixBins];
-    __shared__ uint32_t gbase[kRadixBins];
-    for (int q = threadIdx.x; q < kWarps * kRadixBins; q += blockDim.x) (&h[0][0])[q] = 0;
-    __syncthreads();
-    const int4 c = chunks[blockIdx.x];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const unsigned lt = lanemask_lt();
-    uint64_t k[kRounds];
-    uint32_t v[kRounds];
-    uint32_t rd[kRounds];  // (rank within warp << 9) | digit (digit 256 = empty slot)
-#pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        const int i = w * kPerWarp + r * 32 + lane;
-        const bool valid = i < c.z;
-        unsigned d = kRadixBins;
-        if (valid) {
-            k[r] = kin[c.y + i];
-            v[r] = vin[c.y + i];
-            d = (unsigned)((k[r] >> shift) & (kRadixBins - 1));
-        }
-        const unsigned peers = __match_any_sync(FULL, d);
-        const unsigned before = valid ? h[w][d] : 0u;
-        __syncwarp();
-        if (valid && (peers & lt) == 0) h[w][d] = before + __popc(peers);
-        __syncwarp();
-        rd[r] = ((before + __popc(peers & lt)) << 9) | d;
-    }
-    __syncthreads();
-    const SysStatic S = sys[c.x];
-    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) {
-        uint32_t run = 0;
-        for (int q = 0; q < kWarps; ++q) {
-            const uint32_t t = h[q][d];
-            h[q][d] = run;
-            run += t;
-        }
-        gbase[d] = offs[count_index(S, blockIdx.x, d)];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        const unsigned d = rd[r] & 511u;
-        const bool valid = d < (unsigned)kRadixBins;
-        uint32_t dst = 0;
-        if (valid) {
-            dst = gbase[d] + h[w][d] + (rd[r] >> 9);
-            kout[dst] = k[r];
-            vout[dst] = v[r];
-        }
-        if (next_counts) {
-            // the next pass's histogram: count this key's next digit in the
-            // chunk it lands in (warp-aggregated global atomics)
-            unsigned idx = 0xffffffffu;
-            if (valid) {
-                const int chunk = S.chunk0 + ((int)dst - S.start) / kChunk;
-                const int nd = (int)((k[r] >> (shift + kRadixBits)) & (kRadixBins - 1));
-                idx = count_index(S, chunk, nd);
-            }
-            const unsigned peers = __match_any_sync(FULL, idx);
-            if (valid && (peers & lt) == 0) atomicAdd(&next_counts[idx], (unsigned)__popc(peers));
-        }
-    }
-}
-
-// ---------------------------------------------------------------- scan
-
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = kScanTile / kScanThreads;  // 8
 
@@ -171,6 +97,108 @@ __device__ __forceinline__ uint32_t block_exclusive(uint32_t x, uint32_t *total)
     *total = tot;
     return wbase + inc - x;
 }
+
+// Scatter of one chunk: ranks as in the histogram (stable), then the chunk is
+// laid out in digit order in shared memory and written from there, so
+// neighbouring threads write neighbouring addresses of one digit's run
+// (coalesced), and the next pass's digits are counted per destination chunk.
+// Dynamic shared memory: per-warp counts | global bases | block bases | keys | ids.
+constexpr size_t kScatterSmem = sizeof(uint32_t) * (kWarps * kRadixBins + 2 * kRadixBins) +
+                                sizeof(uint64_t) * kChunk + sizeof(uint32_t) * kChunk;
+
+__global__ void __launch_bounds__(kSortThreads, 2)
+k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+             uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+             const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+             const uint32_t *__restrict__ offs, int shift, uint32_t *__restrict__ next_counts,
+             const Small *__restrict__ sm)
+{
+    if (sm->status) return;
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t(*h)[kRadixBins] = reinterpret_cast<uint32_t(*)[kRadixBins]>(smem);
+    uint32_t *gbase = reinterpret_cast<uint32_t *>(smem) + kWarps * kRadixBins;
+    uint32_t *bstart = gbase + kRadixBins;
+    uint64_t *skey = reinterpret_cast<uint64_t *>(bstart + kRadixBins);
+    uint32_t *sval = reinterpret_cast<uint32_t *>(skey + kChunk);
+    for (int q = threadIdx.x; q < kWarps * kRadixBins; q += blockDim.x) (&h[0][0])[q] = 0;
+    __syncthreads();
+    const int4 c = chunks[blockIdx.x];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned lt = lanemask_lt();
+    uint64_t k[kRounds];
+    uint32_t v[kRounds];
+    uint32_t rd[kRounds];  // (rank within warp << 9) | digit (digit 256 = empty slot)
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const int i = w * kPerWarp + r * 32 + lane;
+        const bool valid = i < c.z;
+        unsigned d = kRadixBins;
+        if (valid) {
+            k[r] = kin[c.y + i];
+            v[r] = vin[c.y + i];
+            d = (unsigned)((k[r] >> shift) & (kRadixBins - 1));
+        }
+        const unsigned peers = __match_any_sync(FULL, d);
+        const unsigned before = valid ? h[w][d] : 0u;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) h[w][d] = before + __popc(peers);
+        __syncwarp();
+        rd[r] = ((before + __popc(peers & lt)) << 9) | d;
+    }
+    __syncthreads();
+    const SysStatic S = sys[c.x];
+    uint32_t total = 0;
+    if (threadIdx.x < kRadixBins) {
+        const int d = threadIdx.x;
+        for (int q = 0; q < kWarps; ++q) {
+            const uint32_t t = h[q][d];
+            h[q][d] = total;
+            total += t;
+        }
+        gbase[d] = offs[count_index(S, blockIdx.x, d)];
+    }
+    uint32_t dummy;
+    const uint32_t bs = block_exclusive(threadIdx.x < kRadixBins ? total : 0u, &dummy);
+    if (threadIdx.x < kRadixBins) bstart[threadIdx.x] = bs;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const unsigned d = rd[r] & 511u;
+        if (d < (unsigned)kRadixBins) {
+            const uint32_t p = bstart[d] + h[w][d] + (rd[r] >> 9);
+            skey[p] = k[r];
+            sval[p] = v[r];
+        }
+    }
+    __syncthreads();
+    for (int q0 = 0; q0 < kChunk; q0 += kSortThreads) {
+        const int q = q0 + threadIdx.x;
+        const bool valid = q < c.z;
+        uint32_t dst = 0;
+        uint64_t key = 0;
+        if (valid) {
+            key = skey[q];
+            const unsigned d = (unsigned)((key >> shift) & (kRadixBins - 1));
+            dst = gbase[d] + ((uint32_t)q - bstart[d]);
+            kout[dst] = key;
+            vout[dst] = sval[q];
+        }
+        if (next_counts) {
+            // the next pass's histogram: count this key's next digit in the
+            // chunk it lands in (warp-aggregated global atomics)
+            unsigned idx = 0xffffffffu;
+            if (valid) {
+                const int chunk = S.chunk0 + ((int)dst - S.start) / kChunk;
+                const int nd = (int)((key >> (shift + kRadixBits)) & (kRadixBins - 1));
+                idx = count_index(S, chunk, nd);
+            }
+            const unsigned peers = __match_any_sync(FULL, idx);
+            if (valid && (peers & lt) == 0) atomicAdd(&next_counts[idx], (unsigned)__popc(peers));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- scan
 
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_reduce(const uint32_t *__restrict__ in, int n, uint32_t *__restrict__ part,
@@ -284,6 +312,14 @@ void launch_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *partials, u
     g_launches += 3;
 }
 
+// Opts the scatter in to more than 48 KiB of dynamic shared memory; called
+// once per context before any launch (and so before any stream capture).
+void prepare_sort_kernels()
+{
+    cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kScatterSmem);
+}
+
 void launch_sort(const BuildBufs &b, cudaStream_t st)
 {
     uint64_t *kin = b.key0, *kout = b.key1;
@@ -299,8 +335,8 @@ void launch_sort(const BuildBufs &b, cudaStream_t st)
         const bool more = pass + 1 < kRadixPasses;
         launch_scan(cur, cur, ncounts, b.scan_part, nullptr, &b.small->status, st);
         if (more) cudaMemsetAsync(nxt, 0, sizeof(uint32_t) * (size_t)ncounts, st);
-        k_rs_scatter<<<b.nchunks, kSortThreads, 0, st>>>(kin, vin, kout, vout, b.chunks, b.sys, cur,
-                                                         shift, more ? nxt : nullptr, b.small);
+        k_rs_scatter<<<b.nchunks, kSortThreads, kScatterSmem, st>>>(
+            kin, vin, kout, vout, b.chunks, b.sys, cur, shift, more ? nxt : nullptr, b.small);
         g_launches += 1;
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;

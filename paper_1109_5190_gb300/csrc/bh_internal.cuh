@@ -185,6 +185,8 @@ void launch_com(const BuildBufs &b, cudaStream_t st);
 void launch_kick(const BuildBufs &b, cudaStream_t st);
 void launch_restore(const BuildBufs &b, cudaStream_t st);
 void launch_validate(const BuildBufs &b, cudaStream_t st);
+void launch_validate_arrays(const float4 *pos, const float4 *vel, int n, Small *sm, int nsm,
+                            cudaStream_t st);
 void launch_diagnostics(const BuildBufs &b, DiagPart *parts, double *out, cudaStream_t st);
 void launch_export(const BuildBufs &b, int sys, bh_node *nodes_dev, float4 *com_dev,
                    uint32_t *order_dev, cudaStream_t st);

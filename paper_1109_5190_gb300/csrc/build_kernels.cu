@@ -581,6 +581,23 @@ k_validate(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&sm->status, ST_BAD_INPUT);
 }
 
+// Input check of one array pair (vel may be null): finite coordinates, mass > 0.
+__global__ void __launch_bounds__(256)
+k_validate_arrays(const float4 *__restrict__ pos, const float4 *__restrict__ vel, int n,
+                  Small *__restrict__ sm)
+{
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 p = pos[i];
+        bad |= !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && p.w > 0.f && isfinite(p.w));
+        if (vel) {
+            const float4 v = vel[i];
+            bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z));
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(&sm->status, ST_BAD_INPUT);
+}
+
 // ------------------------------------------------------ diagnostics (A9)
 
 __global__ void __launch_bounds__(kChunkThreads)
@@ -753,6 +770,13 @@ void launch_restore(const BuildBufs &b, cudaStream_t st)
 void launch_validate(const BuildBufs &b, cudaStream_t st)
 {
     k_validate<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.small);
+    g_launches += 1;
+}
+
+void launch_validate_arrays(const float4 *pos, const float4 *vel, int n, Small *sm, int nsm,
+                            cudaStream_t st)
+{
+    k_validate_arrays<<<nsm * 4, 256, 0, st>>>(pos, vel, n, sm);
     g_launches += 1;
 }
 

@@ -974,13 +974,24 @@ int bh_set_state(bh_system *s, const float *pos_mass, const float *vel, const fl
     if (!s || !pos_mass) return fail(BH_ERR_INVALID, "null argument");
     if (flags & ~BH_DEVICE_PTRS) return fail(BH_ERR_INVALID, "unknown flags");
     TRY(s->f.begin_call());
-    SysState &S = *s->f.systems[0];
-    if (!(flags & BH_DEVICE_PTRS) && !finite_state(S.n, pos_mass, vel))
+    Forest &f = s->f;
+    SysState &S = *f.systems[0];
+    // stage into the step-backup arrays and check there, so a rejected
+    // state leaves the system as it was
+    TRY(upload4(S.bpos(), pos_mass, S.n, flags, f.st));
+    if (vel) TRY(upload4(S.bvel(), vel, S.n, flags, f.st));
+    TRY(f.clear_status());
+    launch_validate_arrays(S.bpos(), vel ? S.bvel() : nullptr, (int)S.n, f.small(), f.nsm, f.st);
+    f.launches += 1;
+    TRY(f.read_small());
+    if (f.h_small->status == ST_BAD_INPUT) {
+        f.clear_status();
         return fail(BH_ERR_INVALID, "non-finite coordinate or non-positive mass");
-    TRY(upload4(S.pos(), pos_mass, S.n, flags, s->f.st));
-    if (vel) TRY(upload4(S.vel(), vel, S.n, flags, s->f.st));
-    if (acc) TRY(upload4(S.acc(), acc, S.n, flags, s->f.st));
-    if (flags & BH_DEVICE_PTRS) TRY(s->f.validate_device());
+    }
+    const size_t nb = (size_t)S.n * sizeof(float4);
+    CKR(cudaMemcpyAsync(S.pos(), S.bpos(), nb, cudaMemcpyDeviceToDevice, f.st));
+    if (vel) CKR(cudaMemcpyAsync(S.vel(), S.bvel(), nb, cudaMemcpyDeviceToDevice, f.st));
+    if (acc) TRY(upload4(S.acc(), acc, S.n, flags, f.st));
     s->f.acc_valid = acc != nullptr;
     s->f.tree_valid = false;
     return s->f.sync();

@@ -391,3 +391,27 @@ def test_large_plummer_sampled():
         assert_accel_close(acc[torch.from_numpy(idx).cuda()].cpu().numpy(), ref, what="C3 step 1")
     finally:
         B.bh_destroy(h)
+
+
+def test_set_state_rejects_bad_input_and_keeps_the_old_state():
+    pm, vel = synth.plummer(2048, 22)
+    h = make(pm, vel)
+    try:
+        a0 = gpu_accel(h, 2048)
+        bad = pm.copy()
+        bad[17, 1] = np.nan
+        with pytest.raises(B.BHError):
+            B.bh_set_state(h, bad, vel)
+        bad = pm.copy()
+        bad[5, 3] = -1.0
+        with pytest.raises(B.BHError):
+            B.bh_set_state(h, bad, vel)
+        x = np.zeros_like(pm)
+        B.bh_get_state(h, x, None, None)
+        assert np.array_equal(x, pm)
+        assert np.array_equal(gpu_accel(h, 2048), a0)
+        # a good state with its acceleration: the next step needs no extra walk
+        B.bh_set_state(h, pm, vel, a0)
+        B.bh_step(h, 1, 1e-3)
+    finally:
+        B.bh_destroy(h)

@@ -376,6 +376,10 @@ def bench_batched(args, B, torch):
         torch.cuda.synchronize()
         t_forest = time.perf_counter() - t0
         _, nodes = B.bh_forest_info(f)
+        # the same graph recaptured with phase events, run once more
+        B.bh_forest_profile_begin(f)
+        B.bh_forest_step(f, args.forest_steps, 1e-3, True)
+        phase_ms, nst, _ = B.bh_forest_profile_end(f)
     finally:
         B.bh_forest_destroy(f)
     batched = n_tot * args.forest_steps / t_forest
@@ -397,6 +401,8 @@ def bench_batched(args, B, torch):
                         "half Plummer / half uniform cold collapse, eps 0.01, theta 0.5, dt 1e-3, seed 4",
             "value": batched, "unit": UNIT, "steps_in_one_graph": args.forest_steps,
             "ms_per_step": 1e3 * t_forest / args.forest_steps, "nodes": nodes,
+            "phase_ms_per_step": {k: float(v) / max(nst, 1) for k, v in
+                                  zip(("integrate", "build", "walk"), phase_ms)},
             "walk_shape": list(shape),
             "plain_sequential": {"value": plain, "unit": UNIT,
                                  "steps_per_system": args.plain_steps,

@@ -250,6 +250,10 @@ int bh_forest_set_tuning(bh_forest *f, const bh_tuning *t);
 int bh_forest_autotune(bh_forest *f, bh_tuning *best);
 /* Total particles and node count of the last build. */
 int bh_forest_info(bh_forest *f, int64_t *n_total, int64_t *n_nodes);
+/* Phase timing of the forest's steps, as bh_profile_begin / bh_profile_end:
+ * phase_ms[BH_NPHASE] sums the device time of each phase over all systems. */
+int bh_forest_profile_begin(bh_forest *f);
+int bh_forest_profile_end(bh_forest *f, double *phase_ms, int64_t *steps, int64_t *launches);
 
 /* ------------------------------------------------------------------ server */
 

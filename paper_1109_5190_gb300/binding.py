@@ -108,6 +108,8 @@ _SIGS = {
     "bh_forest_set_tuning": ([P, P], I),
     "bh_forest_autotune": ([P, P], I),
     "bh_forest_info": ([P, P, P], I),
+    "bh_forest_profile_begin": ([P], I),
+    "bh_forest_profile_end": ([P, P, P, P], I),
     "bh_server_create": ([P, SZ, I, P, U], I),
     "bh_submit": ([P, P, P], I),
     "bh_poll": ([P, C.c_uint64, P], I),
@@ -348,6 +350,18 @@ def bh_forest_info(h):
     a, b = C.c_int64(), C.c_int64()
     _check(lib.bh_forest_info(h, C.byref(a), C.byref(b)))
     return a.value, b.value
+
+
+def bh_forest_profile_begin(h):
+    return _check(lib.bh_forest_profile_begin(h))
+
+
+def bh_forest_profile_end(h):
+    ph = np.zeros(BH_NPHASE, np.float64)
+    steps = C.c_int64()
+    launches = C.c_int64()
+    _check(lib.bh_forest_profile_end(h, ph.ctypes.data, C.byref(steps), C.byref(launches)))
+    return ph, steps.value, launches.value
 
 
 # ------------------------------------------------------------------ server

@@ -1206,6 +1206,19 @@ int bh_forest_info(bh_forest *f, int64_t *n_total, int64_t *n_nodes)
     return BH_OK;
 }
 
+int bh_forest_profile_begin(bh_forest *f)
+{
+    if (!f) return fail(BH_ERR_INVALID, "null forest");
+    f->f.profile_begin();
+    return BH_OK;
+}
+
+int bh_forest_profile_end(bh_forest *f, double *phase_ms, int64_t *steps, int64_t *launches)
+{
+    if (!f) return fail(BH_ERR_INVALID, "null forest");
+    return f->f.profile_end(phase_ms, steps, launches);
+}
+
 // ---------------------------------------------------------- micro-benchmarks
 
 int bh_micro_fma_peak(double *gflops, void *stream)

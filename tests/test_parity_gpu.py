@@ -297,7 +297,10 @@ def test_forest_systems_equal_alone():
     f = B.bh_forest_create(descs)
     try:
         B.bh_forest_compute_accel(f)
+        B.bh_forest_profile_begin(f)
         B.bh_forest_step(f, 3, 1e-3, use_graph=True)
+        phase_ms, nst, launches = B.bh_forest_profile_end(f)
+        assert nst == 3 and launches > 0 and np.all(phase_ms > 0)
         for k, d in enumerate(descs):
             n = len(d["pos_mass"])
             xf = np.zeros((n, 4), np.float32); af = np.zeros((n, 4), np.float32)

@@ -1262,11 +1262,14 @@ struct Job {
     std::unique_ptr<SysState> state;
 };
 
-// Device bytes a resident system needs: its state plus its share of the
-// forest's scratch (keys, ids, sorted copy, counts, ~2 nodes per particle).
+// Device bytes a resident system needs: its state (five float4 arrays) plus
+// its share of the forest's scratch (two key and two id buffers, the sorted
+// copy, node counts and offsets) and of the node arrays (WNode 32 B, nodeR
+// 16 B, nodeD 32 B, level-list entry 4 B; up to ~2 nodes per particle with
+// the growth margin).
 size_t job_bytes(int64_t n)
 {
-    const size_t per = 5 * 16 + (8 + 8 + 4 + 4 + 16 + 4 + 4) + 2 * (16 + 16 + 1 + 4);
+    const size_t per = 5 * 16 + (8 + 8 + 4 + 4 + 16 + 4 + 4) + 2 * (32 + 16 + 32 + 4);
     return (size_t)n * per + 4096 * 64;
 }
 

@@ -347,10 +347,13 @@ def test_server_results_same_alone_and_in_mix():
 
 
 def test_uniform_cube_million_step0_all_particles():
-    # uniform cube N = 2^20, eps = 0.005, theta in {0.5, 0.7}: every particle
-    # against the oracle at step 0, then a seeded 4096 sample after 2 steps
+    # uniform cube N = 2^20, eps = 0.005, theta in {0.5, 0.7}, 20 KDK steps of
+    # dt = 5e-4: every particle against the oracle at step 0, then a seeded
+    # 4096 sample (oracle tree of all particles at the GPU's positions) after
+    # steps 10 and 20
     n = 1 << 20
     pm, vel = synth.uniform_cube(n, 2)
+    idx = np.random.default_rng(20).choice(n, 4096, replace=False)
     for theta in (0.5, 0.7):
         h = make(pm, vel, eps=0.005, theta=theta)
         try:
@@ -358,12 +361,13 @@ def test_uniform_cube_million_step0_all_particles():
             T = oracle.Tree(pm)
             ref, _, _ = T.accel(theta, 0.005)
             assert_accel_close(a, ref, what=f"C2 theta={theta}")
-            B.bh_step(h, 2, 5e-4)
-            x = np.zeros_like(pm); a = np.zeros_like(pm)
-            B.bh_get_state(h, x, None, a)
-            idx = np.random.default_rng(20).choice(n, 4096, replace=False)
-            ref, _, _ = oracle.Tree(x).accel(theta, 0.005, targets=idx)
-            assert_accel_close(a[idx], ref, what=f"C2 step 2 theta={theta}")
+            del T
+            for step in (10, 20):
+                B.bh_step(h, 10, 5e-4)
+                x = np.zeros_like(pm); a = np.zeros_like(pm)
+                B.bh_get_state(h, x, None, a)
+                ref, _, _ = oracle.Tree(x).accel(theta, 0.005, targets=idx)
+                assert_accel_close(a[idx], ref, what=f"C2 step {step} theta={theta}")
         finally:
             B.bh_destroy(h)
 

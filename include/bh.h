@@ -108,7 +108,15 @@ typedef struct bh_node {
  *                   32): 32 = the warp walks the union of its particles'
  *                   traversals (one broadcast node load per step), 4 or 8 =
  *                   aligned lane groups each walk their own union, 1 = every
- *                   lane walks its own particles' traversal */
+ *                   lane walks its own particles' traversal.  0 = split walk
+ *                   (ppl 1): the warp walks the union of the top levels
+ *                   (level <= clamp(floor(log8 n) - 3, 2, 5)), then every lane
+ *                   walks the subtrees below them that it opened on its own.
+ * Accelerations are bit-identical for every shape with group >= 1.  The split
+ * walk sums the same terms in another order, fixed by each particle's tile (32
+ * consecutive sorted particles of its system), so its results are
+ * bit-identical among split shapes, alone or in a forest, and differ from the
+ * others only by rounding; interaction counts are the same for every shape. */
 typedef struct bh_tuning {
     int ppl;
     int warps_per_block;

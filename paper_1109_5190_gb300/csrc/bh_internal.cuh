@@ -31,7 +31,7 @@ constexpr int kChunk = 4096;
 constexpr int kChunkThreads = 256;
 constexpr int kItems = kChunk / kChunkThreads;  // 16
 constexpr float kLeafCrit = -1.0f;
-constexpr float kBucketCrit = -2.0f;
+constexpr float kBucketCrit = __builtin_huge_valf();  // +inf: never accepted as a whole
 constexpr int kRadixBits = 8;
 constexpr int kRadixBins = 1 << kRadixBits;
 constexpr int kRadixPasses = 8;  // 63-bit keys
@@ -98,8 +98,9 @@ struct Small {
 //   a = (hx, hy, hz, mass)   FP32 centre of mass (high part) and mass
 //   b = (crit2 bits, skip, lo_xy, lo_z | e << 16)
 //       crit2 = s^2/theta^2 (accept iff d^2 > crit2), -1 for a one-particle
-//       leaf (always taken as is), -2 for a depth-cap bucket; skip = index of
-//       the next node after the subtree; the low part com - h of each
+//       leaf (always taken as is), +inf for a depth-cap bucket (never taken
+//       as a whole: its particles are summed one by one); skip = index of
+//       the next node after the subtree (> the node's own index); the low part com - h of each
 //       coordinate as an int16 multiple of 2^(e - 127) (e chosen per node
 //       from the largest |h|, so the low part keeps 2^-16 of an FP32 ulp).
 // Fields the walk rarely needs live in nodeR = (first, count, level, 0).

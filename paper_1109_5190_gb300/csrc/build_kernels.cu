@@ -420,8 +420,13 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
                 crit = __fmul_rn(__fmul_rn(sl, sl), S.inv_theta2);
             }
             nodeR[n] = make_int4(j, count, l, 0);
+            // the walk's loop bound: every skip pointer lies past its node and
+            // within the system's nodes (true by construction; checked here so
+            // that the walk itself need not)
+            const unsigned skip = noff[end];
+            if (skip <= n || skip > noff[b]) atomicExch(&sm->status, ST_WALK_LIMIT);
             // low part 0 with scale 2^0 until the centre-of-mass pass fills it
-            nodeW[n].b = make_uint4(__float_as_uint(crit), noff[end], 0u, 127u << 16);
+            nodeW[n].b = make_uint4(__float_as_uint(crit), skip, 0u, 127u << 16);
             if (l >= s.lo && l <= s.hi) {
                 nlist[base[l] + atomicAdd(&h[l], 1u)] = n;
             } else if (l > 0) {  // one-particle leaf: the particle itself
@@ -438,7 +443,7 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
                     const double cx = D.mx[0] / D.mtot, cy = D.mx[1] / D.mtot, cz = D.mx[2] / D.mtot;
                     const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
                     nodeW[n].a = make_float4(hx, hy, hz, (float)D.mtot);
-                    nodeW[n].b = wn_pack(crit, (int)noff[end], cx, cy, cz, hx, hy, hz);
+                    nodeW[n].b = wn_pack(crit, (int)skip, cx, cy, cz, hx, hy, hz);
                     nodeD[n] = make_double4(D.mtot, cx, cy, cz);
                 }
             }

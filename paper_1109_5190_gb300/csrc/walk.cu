@@ -26,14 +26,16 @@
 //     the lane mask such a stack would carry, no stack can overflow, and the
 //     warp visits the union of its particles' traversals in memory order.
 //   * One-particle leaves carry threshold -1 (always accepted as the particle
-//     itself); depth-cap buckets carry -2 and are summed particle by
-//     particle (a warp-uniform branch).
+//     itself); depth-cap buckets carry +inf (never accepted as a whole) and
+//     are summed particle by particle where a walk would open them.
 //   * Compensated (Kahan) FP32 accumulation of each force component (and of
 //     the potential when requested).
 //   * The loop's trip count is bounded by the node count: every iteration
-//     strictly increases the smallest next index.  A skip pointer that does
-//     not move forward means a corrupt tree; the warp then stops and reports
-//     ST_WALK_LIMIT instead of spinning.
+//     strictly increases the smallest next index, because every skip pointer
+//     lies past its node.  The topology pass checks that for each node it
+//     writes (index < skip <= end of the system's nodes); a violation is a
+//     corrupt tree: it sets ST_WALK_LIMIT and no later kernel, the walk
+//     included, runs.
 #include "bh.h"
 #include "bh_internal.cuh"
 
@@ -69,10 +71,15 @@ __device__ __forceinline__ void acc_add(float &s, float &c, float x)
 // rounding distance of the threshold: s^2 < theta^2 d^2 with s = side 2^-level
 // and d from the FP64 centre of mass (the same formula and operation order as
 // the FP64 definition, so both decide alike).
-__device__ __noinline__ bool accept_fp64(const double4 *__restrict__ nodeD,
-                                         const int4 *__restrict__ nodeR, int node, float px,
-                                         float py, float pz, double side, double theta2)
+template <bool INLINE>
+__device__ __forceinline__ bool accept_fp64_body(const double4 *__restrict__ nodeD,
+                                                 const int4 *__restrict__ nodeR,
+                                                 const SysStatic *__restrict__ sys,
+                                                 const SysDyn *__restrict__ dyn, int sysid,
+                                                 int node, float px, float py, float pz)
 {
+    const double side = (double)dyn[sysid].side;
+    const double theta2 = sys[sysid].theta2;
     const int level = nodeR[node].z;
     const double4 D = nodeD[node];
     const double dx = __dsub_rn(D.y, (double)px);
@@ -81,6 +88,15 @@ __device__ __noinline__ bool accept_fp64(const double4 *__restrict__ nodeD,
     const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     const double s = side * __longlong_as_double((long long)(1023 - level) << 52);
     return __dmul_rn(s, s) < __dmul_rn(theta2, d2);
+}
+
+__device__ __noinline__ bool accept_fp64(const double4 *__restrict__ nodeD,
+                                         const int4 *__restrict__ nodeR,
+                                         const SysStatic *__restrict__ sys,
+                                         const SysDyn *__restrict__ dyn, int sysid, int node,
+                                         float px, float py, float pz)
+{
+    return accept_fp64_body<false>(nodeD, nodeR, sys, dyn, sysid, node, px, py, pz);
 }
 
 // Offset within its tile of a lane's k-th particle.  When the whole warp
@@ -121,6 +137,25 @@ __device__ __forceinline__ void interact(float m, float dx, float dy, float dz, 
     acc_add<KAHAN>(az, cz, mi3 * dz);
     if (POT && !self) acc_add<KAHAN>(pp, cp, mi);
     if (COUNT) cnt += 1;
+}
+
+// A depth-cap bucket (equal keys down to level 21) is never taken as a whole:
+// its particles are summed one by one, like the leaves they would be.
+template <bool KAHAN, bool POT, bool COUNT>
+__device__ __forceinline__ void bucket_sum(const int4 *__restrict__ nodeR,
+                                        const float4 *__restrict__ spos, int node, float px,
+                                        float py, float pz, int myj, float eps2, float &ax,
+                                        float &ay, float &az, float &cx, float &cy, float &cz,
+                                        float &pp, float &cp, unsigned &cnt)
+{
+    const int4 R = __ldg(&nodeR[node]);  // first, count
+    for (int q = R.x; q < R.x + R.y; ++q) {
+        const float4 P = __ldg(&spos[q]);
+        const float dx = P.x - px, dy = P.y - py, dz = P.z - pz;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        interact<KAHAN, POT, COUNT>(P.w, dx, dy, dz, d2, eps2, q == myj, ax, ay, az, cx, cy, cz,
+                                    pp, cp, cnt);
+    }
 }
 
 // GROUP = 32: the warp votes (__reduce_min_sync) on the next node and visits
@@ -170,8 +205,6 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
         const int root = (int)a.noff[sstart];
         const int nend = (int)a.noff[sstart + S.n];
         const float eps2 = S.eps2;
-        const double theta2 = S.theta2;
-        const double side = (double)a.dyn[tl.sys].side;
 
         float px[PPL], py[PPL], pz[PPL];
         int nxt[PPL], myj[PPL];
@@ -219,62 +252,47 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
             float4 A;
             uint4 B;
             load_node(a.nodeW + cur, A, B);
+            // skip > cur for every node (checked where the topology pass writes
+            // it), so each step moves forward and the loop ends
             const int skip = wn_skip(B);
-            if (skip <= cur) {  // corrupt skip pointer: report, never spin
-                atomicExch(&sm->status, ST_WALK_LIMIT);
-                break;
-            }
             const float crit = wn_crit(B);
-            if (crit == kBucketCrit) {
-                const int4 R = __ldg(&a.nodeR[cur]);  // first, count
-                for (int q = R.x; q < R.x + R.y; ++q) {
-                    const float4 P = __ldg(&a.spos[q]);
+            // band: negative for leaves (never a tie), infinite for buckets
+            // (whose test always opens: diff = -inf, never inside the band)
+            const float band = crit * kTieBand;
+            // low part of the centre of mass: int16 multiples of a power of two,
+            // folded into the distance by one fused multiply-add per axis
+            // (the product is exact, so this equals adding the decoded value)
+            const float lscale = __int_as_float((int)(B.w >> 16) << 23);
+            const float lqx = (float)(short)(B.z & 0xffffu);
+            const float lqy = (float)(short)(B.z >> 16);
+            const float lqz = (float)(short)(B.w & 0xffffu);
 #pragma unroll
-                    for (int k = 0; k < PPL; ++k) {
-                        if (kSolo || nxt[k] == cur) {
-                            const float dx = P.x - px[k], dy = P.y - py[k], dz = P.z - pz[k];
-                            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                            interact<KAHAN, POT, COUNT>(P.w, dx, dy, dz, d2, eps2, q == myj[k],
-                                                        ax[k], ay[k], az[k], cx[k], cy[k], cz[k],
-                                                        pp[k], cp[k], cnt[k]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < PPL; ++k)
-                    if (kSolo || nxt[k] == cur) nxt[k] = skip;
-            } else {
-                const float band = crit * kTieBand;  // negative for leaves: never a tie
-                // low part of the centre of mass: int16 multiples of a power of two,
-                // folded into the distance by one fused multiply-add per axis
-                // (the product is exact, so this equals adding the decoded value)
-                const float lscale = __int_as_float((int)(B.w >> 16) << 23);
-                const float lqx = (float)(short)(B.z & 0xffffu);
-                const float lqy = (float)(short)(B.z >> 16);
-                const float lqz = (float)(short)(B.w & 0xffffu);
-#pragma unroll
-                for (int k = 0; k < PPL; ++k) {
-                    if (kSolo || nxt[k] == cur) {
-                        // distance to the centre of mass from its high and low parts
-                        const float dx = fmaf(lqx, lscale, A.x - px[k]);
-                        const float dy = fmaf(lqy, lscale, A.y - py[k]);
-                        const float dz = fmaf(lqz, lscale, A.z - pz[k]);
-                        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                        const float diff = d2 - crit;
-                        bool acc = diff > 0.f;
-                        if (fabsf(diff) < band)
-                            acc = accept_fp64(a.nodeD, a.nodeR, cur, px[k], py[k], pz[k], side,
-                                              theta2);
-                        if (acc) {
-                            // the potential leaves out the particle's own leaf
-                            const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[cur].x) == myj[k];
-                            interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self,
-                                                        ax[k], ay[k], az[k], cx[k], cy[k], cz[k],
-                                                        pp[k], cp[k], cnt[k]);
-                            nxt[k] = skip;
-                        } else {
-                            nxt[k] = cur + 1;
-                        }
+            for (int k = 0; k < PPL; ++k) {
+                if (kSolo || nxt[k] == cur) {
+                    // distance to the centre of mass from its high and low parts
+                    const float dx = fmaf(lqx, lscale, A.x - px[k]);
+                    const float dy = fmaf(lqy, lscale, A.y - py[k]);
+                    const float dz = fmaf(lqz, lscale, A.z - pz[k]);
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float diff = d2 - crit;
+                    bool acc = diff > 0.f;
+                    if (fabsf(diff) < band)
+                        acc = accept_fp64(a.nodeD, a.nodeR, a.sys, a.dyn, tl.sys, cur, px[k],
+                                          py[k], pz[k]);
+                    if (acc) {
+                        // the potential leaves out the particle's own leaf
+                        const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[cur].x) == myj[k];
+                        interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self,
+                                                    ax[k], ay[k], az[k], cx[k], cy[k], cz[k],
+                                                    pp[k], cp[k], cnt[k]);
+                        nxt[k] = skip;
+                    } else if (crit == kBucketCrit) {
+                        bucket_sum<KAHAN, POT, COUNT>(a.nodeR, a.spos, cur, px[k], py[k], pz[k],
+                                                      myj[k], eps2, ax[k], ay[k], az[k], cx[k],
+                                                      cy[k], cz[k], pp[k], cp[k], cnt[k]);
+                        nxt[k] = skip;
+                    } else {
+                        nxt[k] = cur + 1;
                     }
                 }
             }
@@ -314,6 +332,220 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
     }
 }
 
+// ---------------------------------------------------------------- split walk
+//
+// The same per-particle decisions and the same interaction set as k_walk, in
+// two phases per tile of 32 particles:
+//   1. the top levels (<= Ltop): the warp votes on the smallest next node
+//      (__reduce_min_sync) and reads it once for all lanes; every lane decides
+//      for itself.  A lane that opens a level-Ltop node does not descend: the
+//      warp appends (first child, subtree end) to its queue in shared memory,
+//      and every lane that opened it sets the entry's bit in its own mask.
+//   2. the levels below: every lane walks the queued subtrees its bit is set
+//      in, one after another, on its own (no vote, no waiting on other lanes).
+// The top levels are where the walks of neighbouring particles coincide
+// (a broadcast load serves the whole warp); below, they diverge, and the lanes
+// stop sharing a schedule.  A full queue is drained (phase 2) before phase 1
+// goes on.  A particle's terms are summed (Kahan) in an order fixed by its
+// tile -- 32 consecutive particles of its system, whatever the launch shape,
+// alone or in a forest -- so results are bit-identical across split shapes.
+constexpr int kSplitQueue = 32;       // queue entries per warp
+constexpr int kSplitMaxWarps = 16;    // warps per block
+
+// Lowest level walked by the warp vote: 3 levels above the depth at which a
+// uniform system has about one particle per cell (floor(log8 n)), within 2..5.
+__device__ __forceinline__ int split_top_level(int n)
+{
+    const int l8 = (31 - __clz(max(n, 1))) / 3;
+    return min(5, max(2, l8 - 3));
+}
+
+// Next tile for the calling warp (lane 0 takes it; every lane gets it):
+// first the block's share of the static range, then the global queue.
+__device__ __forceinline__ int next_tile(const WalkArgs &a, unsigned *s_next, int lane)
+{
+    int t = 0;
+    if (lane == 0) {
+        const int per_block = (int)(((long long)a.ntiles * a.static_share / 100) / gridDim.x);
+        const int k = (int)atomicAdd(s_next, 1u);
+        t = k < per_block ? range_of_block(a.nsm) * per_block + k
+                          : per_block * (int)gridDim.x + (int)atomicAdd(&a.small->queue, 1u);
+    }
+    return __shfl_sync(FULL, t, 0);
+}
+
+template <bool KAHAN, bool POT, bool COUNT>
+__global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
+{
+    __shared__ uint2 s_q[kSplitMaxWarps][kSplitQueue];  // (first child, subtree end)
+    __shared__ unsigned s_next;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    Small *sm = a.small;
+    if (sm->status) return;
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    for (;;) {
+        const int t = next_tile(a, &s_next, lane);
+        if (t >= a.ntiles) break;
+        const Tile tl = a.tiles[t];
+        const int sysid = tl.sys;
+        int root, nend;
+        float eps2, crit_top;
+        {
+            const SysStatic &S = a.sys[sysid];
+            root = (int)a.noff[S.start];
+            nend = (int)a.noff[S.start + S.n];
+            eps2 = S.eps2;
+            // threshold of the level-Ltop nodes, by the topology pass's formula
+            const float sl = __fmul_rn(a.dyn[sysid].side,
+                                       __int_as_float((127 - split_top_level(S.n)) << 23));
+            crit_top = __fmul_rn(__fmul_rn(sl, sl), S.inv_theta2);
+        }
+
+        const int myj = tl.start + lane;
+        const bool live = lane < tl.count;
+        float px = 0.f, py = 0.f, pz = 0.f;
+        if (live) {
+            const float4 P = a.spos[myj];
+            px = P.x; py = P.y; pz = P.z;
+        }
+        float ax = 0.f, ay = 0.f, az = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pp = 0.f, cp = 0.f;
+        unsigned cnt = 0, iters = 0, vis = 0;
+        int nxt = live ? root : nend;
+        int qn = 0;           // warp-uniform
+        unsigned mybits = 0;  // bit k: this lane opened the node of queue entry k
+        bool top_done = false;
+
+        for (;;) {
+            // ---- phase 1: warp-voted walk of the top levels
+            while (qn < kSplitQueue) {
+                const int cur = (int)__reduce_min_sync(FULL, (unsigned)nxt);
+                if (cur >= nend) {
+                    top_done = true;
+                    break;
+                }
+                if (COUNT) ++iters;
+                float4 A;
+                uint4 B;
+                load_node(a.nodeW + cur, A, B);
+                const int skip = wn_skip(B);  // > cur, checked by the topology pass
+                const float crit = wn_crit(B);
+                bool enq = false;
+                if (nxt == cur) {
+                    if (COUNT) ++vis;
+                    const float band = crit * kTieBand;
+                    const float lscale = __int_as_float((int)(B.w >> 16) << 23);
+                    const float dx = fmaf((float)(short)(B.z & 0xffffu), lscale, A.x - px);
+                    const float dy = fmaf((float)(short)(B.z >> 16), lscale, A.y - py);
+                    const float dz = fmaf((float)(short)(B.w & 0xffffu), lscale, A.z - pz);
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float diff = d2 - crit;
+                    bool acc = diff > 0.f;
+                    if (fabsf(diff) < band)
+                        acc = accept_fp64_body<true>(a.nodeD, a.nodeR, a.sys, a.dyn, sysid, cur, px, py, pz);
+                    if (acc) {
+                        const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[cur].x) == myj;
+                        interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az,
+                                                    cx, cy, cz, pp, cp, cnt);
+                        nxt = skip;
+                    } else if (crit == crit_top) {
+                        enq = true;
+                        nxt = skip;
+                    } else if (crit == kBucketCrit) {
+                        bucket_sum<KAHAN, POT, COUNT>(a.nodeR, a.spos, cur, px, py, pz, myj, eps2,
+                                                      ax, ay, az, cx, cy, cz, pp, cp, cnt);
+                        nxt = skip;
+                    } else {
+                        nxt = cur + 1;
+                    }
+                }
+                if (__any_sync(FULL, enq)) {
+                    if (lane == 0) s_q[warp][qn] = make_uint2((unsigned)cur + 1u, (unsigned)skip);
+                    mybits |= (enq ? 1u : 0u) << qn;
+                    ++qn;
+                }
+            }
+            __syncwarp();
+            if (qn > 0) {
+                // ---- phase 2: every lane walks its queued subtrees
+                int n2 = 0, e2 = 0;
+                unsigned it2 = 0;
+                for (;;) {
+                    if (n2 >= e2) {  // next queued subtree of this lane (never empty)
+                        if (!mybits) break;
+                        const uint2 E = s_q[warp][__ffs(mybits) - 1];
+                        mybits &= mybits - 1u;
+                        n2 = (int)E.x;
+                        e2 = (int)E.y;
+                    }
+                    if (COUNT) {
+                        ++it2;
+                        ++vis;
+                    }
+                    float4 A;
+                    uint4 B;
+                    load_node(a.nodeW + n2, A, B);
+                    const int skip = wn_skip(B);  // > n2, checked by the topology pass
+                    const float crit = wn_crit(B);
+                    const float band = crit * kTieBand;
+                    const float lscale = __int_as_float((int)(B.w >> 16) << 23);
+                    const float dx = fmaf((float)(short)(B.z & 0xffffu), lscale, A.x - px);
+                    const float dy = fmaf((float)(short)(B.z >> 16), lscale, A.y - py);
+                    const float dz = fmaf((float)(short)(B.w & 0xffffu), lscale, A.z - pz);
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float diff = d2 - crit;
+                    bool acc = diff > 0.f;
+                    if (fabsf(diff) < band)
+                        acc = accept_fp64_body<true>(a.nodeD, a.nodeR, a.sys, a.dyn, sysid, n2, px, py, pz);
+                    if (acc) {
+                        const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[n2].x) == myj;
+                        interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az,
+                                                    cx, cy, cz, pp, cp, cnt);
+                        n2 = skip;
+                    } else if (crit == kBucketCrit) {
+                        bucket_sum<KAHAN, POT, COUNT>(a.nodeR, a.spos, n2, px, py, pz, myj, eps2,
+                                                      ax, ay, az, cx, cy, cz, pp, cp, cnt);
+                        n2 = skip;
+                    } else {
+                        n2 = n2 + 1;
+                    }
+                }
+                if (COUNT) {
+                    // warp iterations of the phase: the slowest lane's
+                    for (int o = 16; o > 0; o >>= 1) it2 = max(it2, __shfl_xor_sync(FULL, it2, o));
+                    iters += it2;
+                }
+                qn = 0;
+                mybits = 0;
+                __syncwarp();
+            }
+            if (top_done) break;
+        }
+
+        if (COUNT) {
+            unsigned long long ci = live ? cnt : 0u, cv = live ? vis : 0u;
+            for (int o = 16; o > 0; o >>= 1) {
+                ci += __shfl_down_sync(FULL, ci, o);
+                cv += __shfl_down_sync(FULL, cv, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&sm->wstats[0], ci);
+                atomicAdd(&sm->wstats[1], (unsigned long long)iters);
+                atomicAdd(&sm->wstats[2], cv);
+            }
+        }
+        if (live) {
+            const uint32_t v = a.sid[myj];
+            const SysStatic &S = a.sys[sysid];
+            const float G = S.G;
+            if (COUNT) a.counts[v] = cnt;
+            else S.acc[(int)v - S.start] = make_float4(G * ax, G * ay, G * az, POT ? -G * pp : 0.f);
+        }
+        __syncwarp();
+    }
+}
+
 // Blocks of `warps` warps that fit on one SM, queried once per variant and
 // block size (never during stream capture: callers query before capturing).
 template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT>
@@ -332,6 +564,46 @@ int occupancy(int warps)
         cache[warps] = occ > 0 ? occ : -1;
     }
     return cache[warps] > 0 ? cache[warps] : 0;
+}
+
+// The split walk needs its queue and parked sums in shared memory: ask for
+// the smallest carveout that still holds the blocks the registers allow.
+template <bool KAHAN, bool POT, bool COUNT>
+int occupancy_split(int warps)
+{
+    static int cache[33] = {0};
+    if (warps < 1 || warps > kSplitMaxWarps) return 0;
+    if (cache[warps] == 0) {
+        auto *fn = k_walk_split<KAHAN, POT, COUNT>;
+        cudaFuncAttributes fa{};
+        int occ = 0;
+        if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess) {
+            const int regs = fa.numRegs > 0 ? fa.numRegs : 64;
+            const int per_sm = 65536 / (regs * warps * 32);
+            const int want = per_sm < 1 ? 1 : (per_sm > 64 / warps ? 64 / warps : per_sm);
+            const size_t need = (size_t)want * (fa.sharedSizeBytes + 1024) * 100;
+            const int pct = (int)((need + 228 * 1024 - 1) / (228 * 1024));
+            cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 pct > 100 ? 100 : pct);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, warps * 32, 0) != cudaSuccess)
+                occ = 0;
+        }
+        cache[warps] = occ > 0 ? occ : -1;
+    }
+    return cache[warps] > 0 ? cache[warps] : 0;
+}
+
+template <bool KAHAN, bool POT, bool COUNT>
+int launch_split(const WalkArgs *a, const WalkShape &sh, int nsm, cudaStream_t st)
+{
+    if (sh.ppl != 1) return 0;
+    const int occ = occupancy_split<KAHAN, POT, COUNT>(sh.warps);
+    if (occ <= 0) return 0;
+    if (a) {
+        const int bps = sh.blocks_per_sm > 0 ? sh.blocks_per_sm : occ;
+        k_walk_split<KAHAN, POT, COUNT><<<nsm * bps, sh.warps * 32, 0, st>>>(*a);
+    }
+    return occ;
 }
 
 template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT>
@@ -375,6 +647,13 @@ struct Variants {
     static int run(bool kahan, bool pot, const WalkArgs *a, const WalkShape &sh, int nsm,
                    cudaStream_t st)
     {
+        if (sh.group == 0) {  // split walk
+            if (COUNT) return launch_split<true, false, true>(a, sh, nsm, st);
+            if (kahan && pot) return launch_split<true, true, false>(a, sh, nsm, st);
+            if (kahan) return launch_split<true, false, false>(a, sh, nsm, st);
+            if (pot) return launch_split<false, true, false>(a, sh, nsm, st);
+            return launch_split<false, false, false>(a, sh, nsm, st);
+        }
         if (COUNT) {
             if (sh.ppl != 1) return 0;
             switch (sh.group) {

@@ -96,7 +96,7 @@ struct Small {
 
 // The walk's node record: 32 bytes, one DRAM/L2 sector.
 //   a = (hx, hy, hz, mass)   FP32 centre of mass (high part) and mass
-//   b = (crit2 bits, skip, lo_xy, lo_z | e << 16)
+//   b = (crit2 bits, skip, lo_xy, lo_z | e << 23)
 //       crit2 = s^2/theta^2 (accept iff d^2 > crit2), -1 for a one-particle
 //       leaf (always taken as is), +inf for a depth-cap bucket (never taken
 //       as a whole: its particles are summed one by one); skip = index of
@@ -115,7 +115,7 @@ __device__ __forceinline__ int wn_skip(const uint4 &b) { return (int)b.y; }
 
 __device__ __forceinline__ void wn_lo(const uint4 &b, float &lx, float &ly, float &lz)
 {
-    const float scale = __int_as_float((int)(b.w >> 16) << 23);
+    const float scale = __int_as_float(b.w & 0x7f800000u);
     lx = (float)(short)(b.z & 0xffffu) * scale;
     ly = (float)(short)(b.z >> 16) * scale;
     lz = (float)(short)(b.w & 0xffffu) * scale;
@@ -135,7 +135,7 @@ __device__ __forceinline__ uint4 wn_pack(float crit, int skip, double cx, double
     const int qz = max(-32767, min(32767, __double2int_rn((cz - (double)hz) * inv)));
     return make_uint4(__float_as_uint(crit), (unsigned)skip,
                       ((unsigned)qx & 0xffffu) | ((unsigned)qy << 16),
-                      ((unsigned)qz & 0xffffu) | ((unsigned)e << 16));
+                      ((unsigned)qz & 0xffffu) | ((unsigned)e << 23));
 }
 #endif
 

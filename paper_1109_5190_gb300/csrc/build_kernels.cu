@@ -426,7 +426,7 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
             const unsigned skip = noff[end];
             if (skip <= n || skip > noff[b]) atomicExch(&sm->status, ST_WALK_LIMIT);
             // low part 0 with scale 2^0 until the centre-of-mass pass fills it
-            nodeW[n].b = make_uint4(__float_as_uint(crit), skip, 0u, 127u << 16);
+            nodeW[n].b = make_uint4(__float_as_uint(crit), skip, 0u, 127u << 23);
             if (l >= s.lo && l <= s.hi) {
                 nlist[base[l] + atomicAdd(&h[l], 1u)] = n;
             } else if (l > 0) {  // one-particle leaf: the particle itself

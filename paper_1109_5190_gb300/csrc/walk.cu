@@ -67,6 +67,21 @@ __device__ __forceinline__ void acc_add(float &s, float &c, float x)
     }
 }
 
+// s += a * b, compensated: the term's product and the correction carried from
+// the previous step are taken in one fused multiply-add.
+template <bool KAHAN>
+__device__ __forceinline__ void acc_fma(float &s, float &c, float a, float b)
+{
+    if (KAHAN) {
+        const float y = fmaf(a, b, -c);
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    } else {
+        s = fmaf(a, b, s);
+    }
+}
+
 // The paper's opening test in FP64, for a test whose FP32 value lies within
 // rounding distance of the threshold: s^2 < theta^2 d^2 with s = side 2^-level
 // and d from the FP64 centre of mass (the same formula and operation order as
@@ -132,9 +147,9 @@ __device__ __forceinline__ void interact(float m, float dx, float dy, float dz, 
     const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
     const float mi = m * inv;
     const float mi3 = mi * inv * inv;
-    acc_add<KAHAN>(ax, cx, mi3 * dx);
-    acc_add<KAHAN>(ay, cy, mi3 * dy);
-    acc_add<KAHAN>(az, cz, mi3 * dz);
+    acc_fma<KAHAN>(ax, cx, mi3, dx);
+    acc_fma<KAHAN>(ay, cy, mi3, dy);
+    acc_fma<KAHAN>(az, cz, mi3, dz);
     if (POT && !self) acc_add<KAHAN>(pp, cp, mi);
     if (COUNT) cnt += 1;
 }
@@ -262,7 +277,7 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
             // low part of the centre of mass: int16 multiples of a power of two,
             // folded into the distance by one fused multiply-add per axis
             // (the product is exact, so this equals adding the decoded value)
-            const float lscale = __int_as_float((int)(B.w >> 16) << 23);
+            const float lscale = __int_as_float(B.w & 0x7f800000u);
             const float lqx = (float)(short)(B.z & 0xffffu);
             const float lqy = (float)(short)(B.z >> 16);
             const float lqz = (float)(short)(B.w & 0xffffu);
@@ -435,7 +450,7 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
                 if (nxt == cur) {
                     if (COUNT) ++vis;
                     const float band = crit * kTieBand;
-                    const float lscale = __int_as_float((int)(B.w >> 16) << 23);
+                    const float lscale = __int_as_float(B.w & 0x7f800000u);
                     const float dx = fmaf((float)(short)(B.z & 0xffffu), lscale, A.x - px);
                     const float dy = fmaf((float)(short)(B.z >> 16), lscale, A.y - py);
                     const float dz = fmaf((float)(short)(B.w & 0xffffu), lscale, A.z - pz);
@@ -489,7 +504,7 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
                     const int skip = wn_skip(B);  // > n2, checked by the topology pass
                     const float crit = wn_crit(B);
                     const float band = crit * kTieBand;
-                    const float lscale = __int_as_float((int)(B.w >> 16) << 23);
+                    const float lscale = __int_as_float(B.w & 0x7f800000u);
                     const float dx = fmaf((float)(short)(B.z & 0xffffu), lscale, A.x - px);
                     const float dy = fmaf((float)(short)(B.z >> 16), lscale, A.y - py);
                     const float dz = fmaf((float)(short)(B.w & 0xffffu), lscale, A.z - pz);

@@ -86,12 +86,13 @@ __device__ __forceinline__ void acc_fma(float &s, float &c, float a, float b)
 // rounding distance of the threshold: s^2 < theta^2 d^2 with s = side 2^-level
 // and d from the FP64 centre of mass (the same formula and operation order as
 // the FP64 definition, so both decide alike).
-template <bool INLINE>
-__device__ __forceinline__ bool accept_fp64_body(const double4 *__restrict__ nodeD,
-                                                 const int4 *__restrict__ nodeR,
-                                                 const SysStatic *__restrict__ sys,
-                                                 const SysDyn *__restrict__ dyn, int sysid,
-                                                 int node, float px, float py, float pz)
+// Out of line on purpose: the rare FP64 path then keeps its registers (and
+// its FP64 arithmetic) out of the walk loop.
+__device__ __noinline__ bool accept_fp64(const double4 *__restrict__ nodeD,
+                                         const int4 *__restrict__ nodeR,
+                                         const SysStatic *__restrict__ sys,
+                                         const SysDyn *__restrict__ dyn, int sysid, int node,
+                                         float px, float py, float pz)
 {
     const double side = (double)dyn[sysid].side;
     const double theta2 = sys[sysid].theta2;
@@ -103,15 +104,6 @@ __device__ __forceinline__ bool accept_fp64_body(const double4 *__restrict__ nod
     const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     const double s = side * __longlong_as_double((long long)(1023 - level) << 52);
     return __dmul_rn(s, s) < __dmul_rn(theta2, d2);
-}
-
-__device__ __noinline__ bool accept_fp64(const double4 *__restrict__ nodeD,
-                                         const int4 *__restrict__ nodeR,
-                                         const SysStatic *__restrict__ sys,
-                                         const SysDyn *__restrict__ dyn, int sysid, int node,
-                                         float px, float py, float pz)
-{
-    return accept_fp64_body<false>(nodeD, nodeR, sys, dyn, sysid, node, px, py, pz);
 }
 
 // Offset within its tile of a lane's k-th particle.  When the whole warp
@@ -458,7 +450,7 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
                     const float diff = d2 - crit;
                     bool acc = diff > 0.f;
                     if (fabsf(diff) < band)
-                        acc = accept_fp64_body<true>(a.nodeD, a.nodeR, a.sys, a.dyn, sysid, cur, px, py, pz);
+                        acc = accept_fp64(a.nodeD, a.nodeR, a.sys, a.dyn, sysid, cur, px, py, pz);
                     if (acc) {
                         const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[cur].x) == myj;
                         interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az,
@@ -512,7 +504,7 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
                     const float diff = d2 - crit;
                     bool acc = diff > 0.f;
                     if (fabsf(diff) < band)
-                        acc = accept_fp64_body<true>(a.nodeD, a.nodeR, a.sys, a.dyn, sysid, n2, px, py, pz);
+                        acc = accept_fp64(a.nodeD, a.nodeR, a.sys, a.dyn, sysid, n2, px, py, pz);
                     if (acc) {
                         const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[n2].x) == myj;
                         interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az,

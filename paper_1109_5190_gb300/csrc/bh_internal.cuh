@@ -165,7 +165,7 @@ struct BuildBufs {
     uint32_t *noff;       // n_total + 1
     WNode *nodeW;
     int4 *nodeR;
-    double4 *nodeD;
+    double4_32a *nodeD;
     uint32_t *nlist;
     unsigned node_cap;
     Small *small;
@@ -199,7 +199,7 @@ void launch_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *partials,
 struct WalkArgs {
     const WNode *nodeW;
     const int4 *nodeR;
-    const double4 *nodeD;
+    const double4_32a *nodeD;
     const SysDyn *dyn;
     const float4 *spos;
     const uint32_t *sid;  // sorted -> virtual id

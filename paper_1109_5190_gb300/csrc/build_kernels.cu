@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(kChunkThreads)
 k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
              const SysDyn *__restrict__ dyn, const uint64_t *__restrict__ key,
              const uint32_t *__restrict__ noff, const float4 *__restrict__ spos,
-             WNode *__restrict__ nodeW, int4 *__restrict__ nodeR, double4 *__restrict__ nodeD,
+             WNode *__restrict__ nodeW, int4 *__restrict__ nodeR, double4_32a *__restrict__ nodeD,
              uint32_t *__restrict__ nlist, Small *__restrict__ sm)
 {
     if (halted(sm)) return;
@@ -432,19 +432,19 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
             } else if (l > 0) {  // one-particle leaf: the particle itself
                 const float4 p = spos[j];
                 nodeW[n].a = p;
-                nodeD[n] = make_double4(p.w, p.x, p.y, p.z);
+                nodeD[n] = make_double4_32a(p.w, p.x, p.y, p.z);
             }
             if (l == 0) {
                 if (count == 1) {
                     const float4 p = spos[j];
                     nodeW[n].a = p;
-                    nodeD[n] = make_double4(p.w, p.x, p.y, p.z);
+                    nodeD[n] = make_double4_32a(p.w, p.x, p.y, p.z);
                 } else {
                     const double cx = D.mx[0] / D.mtot, cy = D.mx[1] / D.mtot, cz = D.mx[2] / D.mtot;
                     const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
                     nodeW[n].a = make_float4(hx, hy, hz, (float)D.mtot);
                     nodeW[n].b = wn_pack(crit, (int)skip, cx, cy, cz, hx, hy, hz);
-                    nodeD[n] = make_double4(D.mtot, cx, cy, cz);
+                    nodeD[n] = make_double4_32a(D.mtot, cx, cy, cz);
                 }
             }
         }
@@ -461,7 +461,7 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
 // split into an FP32 high part and a packed low part for the walk.
 __device__ __forceinline__ void com_node(unsigned n, const float4 *__restrict__ spos,
                                          WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR,
-                                         double4 *__restrict__ nodeD)
+                                         double4_32a *__restrict__ nodeD)
 {
     const int4 C = nodeR[n];  // first, count, level
     const uint4 B = nodeW[n].b;
@@ -479,7 +479,7 @@ __device__ __forceinline__ void com_node(unsigned n, const float4 *__restrict__ 
         }
     } else {
         for (int ch = (int)n + 1; ch < skip; ch = wn_skip(nodeW[ch].b)) {
-            const double4 d = nodeD[ch];
+            const double4_32a d = nodeD[ch];
             M += d.x;
             sx += d.x * d.y;
             sy += d.x * d.z;
@@ -489,7 +489,7 @@ __device__ __forceinline__ void com_node(unsigned n, const float4 *__restrict__ 
     const double inv = 1.0 / M;
     const double cx = sx * inv, cy = sy * inv, cz = sz * inv;
     const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
-    nodeD[n] = make_double4(M, cx, cy, cz);
+    nodeD[n] = make_double4_32a(M, cx, cy, cz);
     nodeW[n].a = make_float4(hx, hy, hz, (float)M);
     nodeW[n].b = wn_pack(crit, skip, cx, cy, cz, hx, hy, hz);
 }
@@ -497,7 +497,7 @@ __device__ __forceinline__ void com_node(unsigned n, const float4 *__restrict__ 
 // One level, all blocks.
 __global__ void __launch_bounds__(256)
 k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
-            WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4 *__restrict__ nodeD,
+            WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4_32a *__restrict__ nodeD,
             const Small *__restrict__ sm)
 {
     if (halted(sm)) return;
@@ -511,7 +511,7 @@ k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict_
 // barrier separates the levels, so one launch replaces many near-empty ones.
 __global__ void __launch_bounds__(1024)
 k_com_deep(int l_hi, int l_lo, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
-           WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4 *__restrict__ nodeD,
+           WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4_32a *__restrict__ nodeD,
            const Small *__restrict__ sm)
 {
     if (halted(sm)) return;

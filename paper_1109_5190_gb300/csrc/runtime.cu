@@ -288,7 +288,7 @@ struct Forest {
         b.noff = noff.as<uint32_t>();
         b.nodeW = nodeW.as<WNode>();
         b.nodeR = nodeR.as<int4>();
-        b.nodeD = nodeD.as<double4>();
+        b.nodeD = nodeD.as<double4_32a>();
         b.nlist = nlist.as<uint32_t>();
         b.node_cap = node_cap;
         b.small = small();
@@ -303,7 +303,7 @@ struct Forest {
         if (cap <= node_cap && nodeW.p) return BH_OK;
         TRY(nodeW.ensure(cap * sizeof(WNode)));
         TRY(nodeR.ensure(cap * sizeof(int4)));
-        TRY(nodeD.ensure(cap * sizeof(double4)));
+        TRY(nodeD.ensure(cap * sizeof(double4_32a)));
         TRY(nlist.ensure(cap * sizeof(uint32_t)));
         node_cap = (unsigned)cap;
         invalidate_graph();
@@ -442,7 +442,7 @@ struct Forest {
         WalkArgs a;
         a.nodeW = nodeW.as<WNode>();
         a.nodeR = nodeR.as<int4>();
-        a.nodeD = nodeD.as<double4>();
+        a.nodeD = nodeD.as<double4_32a>();
         a.dyn = d_dyn.as<SysDyn>();
         a.spos = spos.as<float4>();
         a.sid = val0.as<uint32_t>();

@@ -88,7 +88,7 @@ __device__ __forceinline__ void acc_fma(float &s, float &c, float a, float b)
 // the FP64 definition, so both decide alike).
 // Out of line on purpose: the rare FP64 path then keeps its registers (and
 // its FP64 arithmetic) out of the walk loop.
-__device__ __noinline__ bool accept_fp64(const double4 *__restrict__ nodeD,
+__device__ __noinline__ bool accept_fp64(const double4_32a *__restrict__ nodeD,
                                          const int4 *__restrict__ nodeR,
                                          const SysStatic *__restrict__ sys,
                                          const SysDyn *__restrict__ dyn, int sysid, int node,
@@ -97,7 +97,7 @@ __device__ __noinline__ bool accept_fp64(const double4 *__restrict__ nodeD,
     const double side = (double)dyn[sysid].side;
     const double theta2 = sys[sysid].theta2;
     const int level = nodeR[node].z;
-    const double4 D = nodeD[node];
+    const double4_32a D = nodeD[node];
     const double dx = __dsub_rn(D.y, (double)px);
     const double dy = __dsub_rn(D.z, (double)py);
     const double dz = __dsub_rn(D.w, (double)pz);

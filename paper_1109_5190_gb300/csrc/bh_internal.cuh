@@ -30,6 +30,11 @@ constexpr int kNumLevels = kLevels + 1;
 constexpr int kChunk = 4096;
 constexpr int kChunkThreads = 256;
 constexpr int kItems = kChunk / kChunkThreads;  // 16
+// kernels whose per-particle work is a chain of dependent loads (topology,
+// keys, permutation, closing kick) run more threads per chunk, each with fewer
+// particles; those that end in a block reduction keep kChunkThreads
+constexpr int kWideThreads = 1024;
+constexpr int kWideItems = kChunk / kWideThreads;  // 4
 constexpr float kLeafCrit = -1.0f;
 constexpr float kBucketCrit = __builtin_huge_valf();  // +inf: never accepted as a whole
 constexpr int kRadixBits = 8;

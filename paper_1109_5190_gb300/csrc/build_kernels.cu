@@ -212,7 +212,7 @@ __device__ __forceinline__ uint64_t spread3(uint32_t v)
 
 // Key of every particle in input order, value = its virtual id, so the stable
 // radix sort orders equal keys by input index.
-__global__ void __launch_bounds__(kChunkThreads)
+__global__ void __launch_bounds__(kWideThreads)
 k_keys(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
        const SysDyn *__restrict__ dyn, uint64_t *__restrict__ key, uint32_t *__restrict__ val,
        const Small *__restrict__ sm)
@@ -222,8 +222,8 @@ k_keys(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
     const SysStatic S = sys[c.x];
     const SysDyn D = dyn[c.x];
     const int loc0 = c.y - S.start;
-    for (int k = 0; k < kItems; ++k) {
-        const int i = k * kChunkThreads + threadIdx.x;
+    for (int k = 0; k < kWideItems; ++k) {
+        const int i = k * kWideThreads + threadIdx.x;
         if (i >= c.z) break;
         const float4 p = S.pos[loc0 + i];
         const uint32_t qx = quantise(p.x, D.lo[0], D.scale);
@@ -236,7 +236,7 @@ k_keys(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
 
 // ----------------------------------------------------------- permute (A4)
 
-__global__ void __launch_bounds__(kChunkThreads)
+__global__ void __launch_bounds__(kWideThreads)
 k_permute(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
           const uint32_t *__restrict__ sid, float4 *__restrict__ spos,
           const Small *__restrict__ sm)
@@ -244,8 +244,8 @@ k_permute(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
     if (halted(sm)) return;
     const int4 c = chunks[blockIdx.x];
     const SysStatic S = sys[c.x];
-    for (int k = 0; k < kItems; ++k) {
-        const int i = k * kChunkThreads + threadIdx.x;
+    for (int k = 0; k < kWideItems; ++k) {
+        const int i = k * kWideThreads + threadIdx.x;
         if (i >= c.z) break;
         const int j = c.y + i;
         spos[j] = __ldg(&S.pos[(int)sid[j] - S.start]);
@@ -295,7 +295,7 @@ __device__ __forceinline__ Span node_span(const uint64_t *__restrict__ key, int 
     return s;
 }
 
-__global__ void __launch_bounds__(kChunkThreads)
+__global__ void __launch_bounds__(kWideThreads)
 k_topo_count(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
              const uint64_t *__restrict__ key, uint32_t *__restrict__ ncount,
              Small *__restrict__ sm)
@@ -306,8 +306,8 @@ k_topo_count(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
     __syncthreads();
     const int4 c = chunks[blockIdx.x];
     const SysStatic S = sys[c.x];
-    for (int k = 0; k < kItems; ++k) {
-        const int i = k * kChunkThreads + threadIdx.x;
+    for (int k = 0; k < kWideItems; ++k) {
+        const int i = k * kWideThreads + threadIdx.x;
         if (i >= c.z) break;
         const int j = c.y + i;
         const Span s = node_span(key, j, S.start, S.start + S.n);
@@ -367,7 +367,7 @@ __device__ __forceinline__ float pow2_neg(int l) { return __int_as_float((127 - 
 // threshold, plus its slot in its level's list.  The root's centre of mass
 // comes from the FP64 reduction (or the particle itself for a one-particle
 // system); every other centre of mass is written by the bottom-up pass.
-__global__ void __launch_bounds__(kChunkThreads)
+__global__ void __launch_bounds__(kWideThreads)
 k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
              const SysDyn *__restrict__ dyn, const uint64_t *__restrict__ key,
              const uint32_t *__restrict__ noff, const float4 *__restrict__ spos,
@@ -381,8 +381,8 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
     const int4 c = chunks[blockIdx.x];
     const SysStatic S = sys[c.x];
     const int a = S.start, b = S.start + S.n;
-    for (int k = 0; k < kItems; ++k) {
-        const int i = k * kChunkThreads + threadIdx.x;
+    for (int k = 0; k < kWideItems; ++k) {
+        const int i = k * kWideThreads + threadIdx.x;
         if (i >= c.z) break;
         const Span s = node_span(key, c.y + i, a, b);
         for (int l = s.lo; l <= s.hi; ++l) atomicAdd(&h[l], 1u);
@@ -396,8 +396,8 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
     }
     __syncthreads();
     const SysDyn D = dyn[c.x];
-    for (int k = 0; k < kItems; ++k) {
-        const int i = k * kChunkThreads + threadIdx.x;
+    for (int k = 0; k < kWideItems; ++k) {
+        const int i = k * kWideThreads + threadIdx.x;
         if (i >= c.z) break;
         const int j = c.y + i;
         const Span s = node_span(key, j, a, b);
@@ -526,7 +526,7 @@ k_com_deep(int l_hi, int l_lo, const uint32_t *__restrict__ nlist, const float4 
 
 // ------------------------------------------------------ closing kick (A8)
 
-__global__ void __launch_bounds__(kChunkThreads)
+__global__ void __launch_bounds__(kWideThreads)
 k_kick(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
        const int *__restrict__ mode, Small *__restrict__ sm)
 {
@@ -536,8 +536,8 @@ k_kick(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
     if (mode[c.x] != MODE_KDK) return;
     const SysStatic S = sys[c.x];
     const int loc0 = c.y - S.start;
-    for (int k = 0; k < kItems; ++k) {
-        const int i = k * kChunkThreads + threadIdx.x;
+    for (int k = 0; k < kWideItems; ++k) {
+        const int i = k * kWideThreads + threadIdx.x;
         if (i >= c.z) break;
         const int li = loc0 + i;
         float4 v = S.vel[li];
@@ -550,7 +550,7 @@ k_kick(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
 }
 
 // Rolls back the opening kick/drift of a step that overflowed the node buffer.
-__global__ void __launch_bounds__(kChunkThreads)
+__global__ void __launch_bounds__(kWideThreads)
 k_restore(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
           const int *__restrict__ mode)
 {
@@ -558,8 +558,8 @@ k_restore(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
     if (mode[c.x] != MODE_KDK) return;
     const SysStatic S = sys[c.x];
     const int loc0 = c.y - S.start;
-    for (int k = 0; k < kItems; ++k) {
-        const int i = k * kChunkThreads + threadIdx.x;
+    for (int k = 0; k < kWideItems; ++k) {
+        const int i = k * kWideThreads + threadIdx.x;
         if (i >= c.z) break;
         S.pos[loc0 + i] = S.bpos[loc0 + i];
         S.vel[loc0 + i] = S.bvel[loc0 + i];
@@ -722,23 +722,23 @@ void launch_kick_drift_bbox(const BuildBufs &b, cudaStream_t st)
 
 void launch_keys(const BuildBufs &b, cudaStream_t st)
 {
-    k_keys<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.dyn, b.key0, b.val0, b.small);
+    k_keys<<<b.nchunks, kWideThreads, 0, st>>>(b.chunks, b.sys, b.dyn, b.key0, b.val0, b.small);
     g_launches += 1;
 }
 
 void launch_permute(const BuildBufs &b, cudaStream_t st)
 {
-    k_permute<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.val0, b.spos, b.small);
+    k_permute<<<b.nchunks, kWideThreads, 0, st>>>(b.chunks, b.sys, b.val0, b.spos, b.small);
     g_launches += 1;
 }
 
 void launch_topology(const BuildBufs &b, cudaStream_t st)
 {
-    k_topo_count<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.key0, b.ncount, b.small);
+    k_topo_count<<<b.nchunks, kWideThreads, 0, st>>>(b.chunks, b.sys, b.key0, b.ncount, b.small);
     g_launches += 1;
     launch_scan(b.ncount, b.noff, b.n_total, b.scan_part, b.noff + b.n_total, &b.small->status, st);
     k_level_offsets<<<1, 32, 0, st>>>(b.small, b.noff, b.n_total, b.node_cap);
-    k_topo_write<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.dyn, b.key0, b.noff,
+    k_topo_write<<<b.nchunks, kWideThreads, 0, st>>>(b.chunks, b.sys, b.dyn, b.key0, b.noff,
                                                       b.spos, b.nodeW, b.nodeR, b.nodeD, b.nlist,
                                                       b.small);
     g_launches += 2;
@@ -762,13 +762,13 @@ void launch_com(const BuildBufs &b, cudaStream_t st)
 
 void launch_kick(const BuildBufs &b, cudaStream_t st)
 {
-    k_kick<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.mode, b.small);
+    k_kick<<<b.nchunks, kWideThreads, 0, st>>>(b.chunks, b.sys, b.mode, b.small);
     g_launches += 1;
 }
 
 void launch_restore(const BuildBufs &b, cudaStream_t st)
 {
-    k_restore<<<b.nchunks, kChunkThreads, 0, st>>>(b.chunks, b.sys, b.mode);
+    k_restore<<<b.nchunks, kWideThreads, 0, st>>>(b.chunks, b.sys, b.mode);
     g_launches += 1;
 }
 

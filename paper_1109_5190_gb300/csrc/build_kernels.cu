@@ -746,7 +746,7 @@ void launch_topology(const BuildBufs &b, cudaStream_t st)
 
 void launch_com(const BuildBufs &b, cudaStream_t st)
 {
-    const int grid = b.nsm * 2;
+    const int grid = b.nsm * 8;  // full occupancy: short per-thread chains of child loads
     int l = kLevels;
     if (b.deep_cut <= kLevels) {
         k_com_deep<<<1, 1024, 0, st>>>(kLevels, b.deep_cut, b.nlist, b.spos, b.nodeW, b.nodeR,

@@ -639,7 +639,7 @@ struct Forest {
     // Deep levels whose nodes sum to at most kDeepNodes go to one launch.
     void choose_deep_cut()
     {
-        constexpr unsigned kDeepNodes = 16384;
+        constexpr unsigned kDeepNodes = 512;
         if (!adaptive_deep) return;
         unsigned sum = 0;
         int cut = kNumLevels;

@@ -155,10 +155,12 @@ def test_kepler_two_body_closed_form():
         B.bh_destroy(h)
 
 
-def test_potential_and_diagnostics():
+@pytest.mark.parametrize("group", [1, 32, 0])
+def test_potential_and_diagnostics(group):
     pm, vel = synth.plummer(4096, 14)
     h = make(pm, vel, eps=0.01, theta=0.5, flags=B.BH_POTENTIAL)
     try:
+        B.bh_set_tuning(h, 1, 8, 0, group, 75)
         a = gpu_accel(h, 4096)
         ref, pot, _ = oracle.Tree(pm).accel(0.5, 0.01)
         assert_accel_close(a, ref)
@@ -303,7 +305,10 @@ def test_device_pointers_and_torch_stream():
         B.bh_create(B.params(), bad, d_vel)
 
 
-def test_forest_systems_equal_alone():
+@pytest.mark.parametrize("group", [1, 0])
+def test_forest_systems_equal_alone(group):
+    # group 1: one particle per lane; group 0: the split walk, whose sum order
+    # is fixed by each particle's tile, which is the same alone or in a forest
     systems = synth.forest_systems(12, 256, 6000, seed=19, theta=0.5, eps=0.01)
     descs = [dict(pos_mass=s.pos_mass, vel=s.vel, eps=s.eps, theta=s.theta, dt=1e-3) for s in systems]
     # give two systems other parameters: per-system theta / eps / G
@@ -312,6 +317,7 @@ def test_forest_systems_equal_alone():
     descs[7]["G"] = 2.5
     f = B.bh_forest_create(descs)
     try:
+        B.bh_forest_set_tuning(f, 1, 8, 0, group, 0)
         B.bh_forest_compute_accel(f)
         B.bh_forest_profile_begin(f)
         B.bh_forest_step(f, 3, 1e-3, use_graph=True)
@@ -323,6 +329,7 @@ def test_forest_systems_equal_alone():
             B.bh_forest_get_state(f, k, xf, None, af)
             h = make(d["pos_mass"], d["vel"], d["eps"], d["theta"], d.get("G", 1.0))
             try:
+                B.bh_set_tuning(h, 1, 16, 0, group, 75)
                 B.bh_step(h, 3, 1e-3)
                 x1 = np.zeros_like(xf); a1 = np.zeros_like(af)
                 B.bh_get_state(h, x1, None, a1)

@@ -125,19 +125,16 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     const int4 c = chunks[blockIdx.x];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned lt = lanemask_lt();
-    uint64_t k[kRounds];
-    uint32_t v[kRounds];
+    // only (rank, digit) stays in registers between the two phases; keys and
+    // ids are read again (L2 hits) when staged: the block runs at 32
+    // registers per thread, and holding them would spill to local memory
     uint32_t rd[kRounds];  // (rank within warp << 9) | digit (digit 256 = empty slot)
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
         const int i = w * kPerWarp + r * 32 + lane;
         const bool valid = i < c.z;
         unsigned d = kRadixBins;
-        if (valid) {
-            k[r] = kin[c.y + i];
-            v[r] = vin[c.y + i];
-            d = (unsigned)((k[r] >> shift) & (kRadixBins - 1));
-        }
+        if (valid) d = (unsigned)((kin[c.y + i] >> shift) & (kRadixBins - 1));
         const unsigned peers = __match_any_sync(FULL, d);
         const unsigned before = valid ? h[w][d] : 0u;
         __syncwarp();
@@ -165,9 +162,10 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
     for (int r = 0; r < kRounds; ++r) {
         const unsigned d = rd[r] & 511u;
         if (d < (unsigned)kRadixBins) {
+            const int i = w * kPerWarp + r * 32 + lane;
             const uint32_t p = bstart[d] + h[w][d] + (rd[r] >> 9);
-            skey[p] = k[r];
-            sval[p] = v[r];
+            skey[p] = kin[c.y + i];
+            sval[p] = vin[c.y + i];
         }
     }
     __syncthreads();

@@ -141,13 +141,26 @@ def combine_ranks(local_ms: float, units_per_rank: int, steps: int, device=None)
     return t_max, ws * units_per_rank * steps / (t_max * 1e-3)
 
 
-def walk_sources_sha() -> str:
+def code_digest(texts) -> str:
+    """SHA-256 of C/CUDA sources with comments and whitespace removed, so that
+    it changes with the code and not with its comments."""
     import hashlib
+    import re
     h = hashlib.sha256()
-    for f in ("walk.cu", "bh_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1109_5190_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for t in texts:
+        t = re.sub(r"/\*.*?\*/", "", t, flags=re.S)
+        t = re.sub(r"//[^\n]*", "", t)
+        h.update(re.sub(r"\s+", "", t).encode())
     return h.hexdigest()
+
+
+def walk_sources_sha() -> str:
+    """Code digest of the walk's sources (walk.cu and the shared header)."""
+    texts = []
+    for f in ("walk.cu", "bh_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1109_5190_gb300", "csrc", f)) as fh:
+            texts.append(fh.read())
+    return code_digest(texts)
 
 
 def walk_traffic():

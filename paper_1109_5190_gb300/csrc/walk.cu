@@ -7,24 +7,28 @@
 // s^2 < theta^2 d^2 (Section III, Fig. 1, with r the cell side); otherwise
 // its children are visited.  The decision is taken per particle, exactly.
 //
-// GPU design (sm_103a, FP32 ALU-bound; no tensor cores: this is not a dense
-// contraction):
+// GPU design (sm_103a; bound by the L1 load path and instruction issue, not
+// by FP32 math; no tensor cores: this is not a dense contraction):
 //   * Persistent kernel; each warp pulls tiles of 32*PPL consecutive
 //     Morton-sorted particles: first from its block's contiguous share of a
 //     tunable fraction of the tiles (neighbouring walks share L1), then from
 //     an atomic queue over the rest (dynamic load balancing in place of the
 //     paper's runtime work queues, Section III).
-//   * Warp-cooperative traversal: nodes are stored in depth-first pre-order
-//     with a skip pointer (the first node after the subtree).  Each particle
-//     slot keeps the index of the next node it must visit (the root at
-//     first).  The warp votes with __reduce_min_sync for the smallest such
-//     index, loads that node once (a broadcast load shared by all lanes) and
-//     every slot whose next index equals it takes its own decision: accept
-//     (interact, jump to the skip pointer) or open (continue at the next
-//     node, its first child).  The vote replaces an explicit per-warp
-//     (node, lane-mask) stack: the set of slots waiting on a node is exactly
-//     the lane mask such a stack would carry, no stack can overflow, and the
-//     warp visits the union of its particles' traversals in memory order.
+//   * Stackless traversal: nodes are stored in depth-first pre-order with a
+//     skip pointer (the first node after the subtree).  Each particle slot
+//     keeps the index of the next node it must visit (the root at first);
+//     accepting continues at the skip pointer, opening at the next node (the
+//     first child).
+//   * Lanes vote on the next node in aligned groups of GROUP lanes.  GROUP 1:
+//     no vote, every lane walks its own particle (the usual choice: the lanes
+//     of a tile start together and share most node loads).  GROUP 32: the
+//     warp takes the smallest next index (__reduce_min_sync), reads that node
+//     once for all lanes, and every slot waiting on it decides for itself --
+//     the union of the tile's walks.  The vote replaces an explicit per-warp
+//     (node, lane-mask) stack: the slots waiting on a node are exactly the
+//     mask such a stack would carry, and no stack can overflow.
+//   * k_walk_split (below) votes over the top levels only and walks the rest
+//     lane by lane.
 //   * One-particle leaves carry threshold -1 (always accepted as the particle
 //     itself); depth-cap buckets carry +inf (never accepted as a whole) and
 //     are summed particle by particle where a walk would open them.

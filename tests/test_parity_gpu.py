@@ -380,6 +380,7 @@ def test_uniform_cube_million_step0_all_particles():
     for theta in (0.5, 0.7):
         h = make(pm, vel, eps=0.005, theta=theta)
         try:
+            B.bh_autotune(h)  # the walk shape the benchmark times
             a = gpu_accel(h, n)
             T = oracle.Tree(pm)
             ref, _, _ = T.accel(theta, 0.005)
@@ -407,6 +408,7 @@ def test_large_plummer_sampled():
     h = B.bh_create(B.params(1.0, 0.002, 0.6), d_pm, d_vel)
     del d_pm, d_vel
     try:
+        B.bh_autotune(h)  # the walk shape the benchmark times
         idx = np.random.default_rng(21).choice(n, 4096, replace=False)
         acc = torch.zeros((n, 4), dtype=torch.float32, device="cuda")
         B.bh_compute_accel(h, acc)
@@ -445,3 +447,29 @@ def test_set_state_rejects_bad_input_and_keeps_the_old_state():
         B.bh_step(h, 1, 1e-3)
     finally:
         B.bh_destroy(h)
+
+
+@pytest.mark.slow
+def test_forest_512_systems_sampled():
+    # configs[3] at full size: 512 systems (N log-uniform in [256, 65536], half
+    # Plummer, half uniform cold collapse, eps 0.01, theta 0.5), autotuned as
+    # the benchmark runs it; 8 seeded systems against the FP64 oracle, every
+    # particle, after the force evaluation and after one KDK step
+    systems = synth.forest_systems(512, 256, 65536, seed=4, theta=0.5, eps=0.01)
+    descs = [dict(pos_mass=s.pos_mass, vel=s.vel, eps=s.eps, theta=s.theta, dt=1e-3) for s in systems]
+    f = B.bh_forest_create(descs)
+    try:
+        B.bh_forest_compute_accel(f)
+        B.bh_forest_autotune(f)
+        pick = np.random.default_rng(23).choice(len(descs), 8, replace=False)
+        for stage in ("accel", "step"):
+            if stage == "step":
+                B.bh_forest_step(f, 1, 1e-3, use_graph=True)
+            for k in pick:
+                n = len(descs[k]["pos_mass"])
+                x = np.zeros((n, 4), np.float32); a = np.zeros((n, 4), np.float32)
+                B.bh_forest_get_state(f, int(k), x, None, a)
+                ref, _, _ = oracle.Tree(x).accel(0.5, 0.01)
+                assert_accel_close(a, ref, what=f"forest system {k} ({stage})")
+    finally:
+        B.bh_forest_destroy(f)

@@ -244,6 +244,80 @@ def test_error_decreases_as_theta_decreases(oracle_lib):
     assert errs[-1] < 1e-4
 
 
+def _frontier_accel(pm, theta, eps, lo_side):
+    """The Barnes-Hut sum from its set definition, without recursion: particle
+    i uses every node whose proper ancestors all fail the opening test s^2 <
+    theta^2 d^2 for i while the node itself passes it, is a one-particle leaf,
+    or is a depth-cap bucket (then each member particle).  Nodes by brute-force
+    enumeration; centres of mass as direct sums over member particles."""
+    nodes, order = _brute_force_nodes(pm)
+    x = pm[order, :3]
+    m = pm[order, 3]
+    side = float(lo_side[1])
+    com = {}
+    for (lvl, pre, first, cnt, _) in nodes:
+        mm = m[first:first + cnt]
+        com[(lvl, pre)] = (mm.sum(), (mm[:, None] * x[first:first + cnt]).sum(0) / mm.sum())
+    n = len(pm)
+    acc = np.zeros((n, 3)); pot = np.zeros(n); count = np.zeros(n, np.int64)
+    for i in range(n):
+        xi = x[i]
+
+        def opens(lvl, pre, cnt):
+            if cnt == 1 or lvl == 21:
+                return False
+            M, c = com[(lvl, pre)]
+            s = side * 2.0 ** -lvl
+            return not (s * s < theta * theta * float(((c - xi) ** 2).sum()))
+
+        info = {(lvl, pre): cnt for (lvl, pre, first, cnt, _) in nodes}
+        for (lvl, pre, first, cnt, _) in nodes:
+            if opens(lvl, pre, cnt):
+                continue
+            if not all(opens(l2, pre >> (3 * (lvl - l2)), info[(l2, pre >> (3 * (lvl - l2)))])
+                       for l2 in range(lvl)):
+                continue
+            members = range(first, first + cnt) if (cnt == 1 or lvl == 21) else None
+            terms = [(m[j], x[j], j == i) for j in members] if members is not None else \
+                [(com[(lvl, pre)][0], com[(lvl, pre)][1], False)]
+            for (mj, xj, self_term) in terms:
+                d = xj - xi
+                r2 = float((d ** 2).sum()) + eps * eps
+                count[i] += 1
+                if r2 > 0.0:
+                    acc[i] += mj * d / r2 ** 1.5
+                    if not self_term:
+                        pot[i] -= mj / np.sqrt(r2)
+    out_a = np.zeros_like(acc); out_p = np.zeros_like(pot); out_c = np.zeros_like(count)
+    out_a[order] = acc; out_p[order] = pot; out_c[order] = count
+    return out_a, out_p, out_c
+
+
+@pytest.mark.parametrize("kind,n,seed", [("gauss", 40, 11), ("clustered", 60, 12),
+                                         ("planar", 50, 13), ("dups", 30, 14)])
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.7, 1.0])
+def test_walk_equals_set_definition(oracle_lib, kind, n, seed, theta):
+    # theta > 0: the recursive walk against the set definition of the sum it
+    # computes, on inputs small enough to enumerate every node and ancestor
+    if kind == "dups":
+        pm, _ = synth.random_cloud(n, seed, "gauss")
+        pm = pm.astype(np.float64)
+        pm[4:10, :3] = pm[2, :3]      # a bucket of 7 coincident points
+    else:
+        pm, _ = synth.random_cloud(n, seed, kind)
+        pm = pm.astype(np.float64)
+    pm[:, 3] *= np.linspace(0.5, 1.5, n)  # unequal masses: a centroid is not the COM
+    eps = 0.01
+    T = oracle.Tree(pm)
+    a, p, c = T.accel(theta, eps)
+    lo, side = T.cube()
+    wa, wp, wc = _frontier_accel(pm, theta, eps, (lo, side))
+    assert np.array_equal(c, wc)
+    scale = np.abs(wa).max()
+    assert np.abs(a - wa).max() <= 1e-12 * scale
+    assert np.abs(p - wp).max() <= 1e-12 * np.abs(wp).max()
+
+
 def test_fig2_two_inputs_for_remote_particles(oracle_lib):
     # Fig. 2 (Section III): four particles in a 2-D domain; P3 and P4 cluster in
     # node N2, so P1 and P2 each need only two inputs (the other remote

@@ -468,18 +468,21 @@ def bench_large(args, B, torch, fma_peak_tflops, hbm_gbs):
                                "frac": build_gbs / hbm_gbs}}
 
 
-def bench_served(args, B, torch):
-    """Poisson request stream (200 requests/s; each request a Plummer or
-    uniform system of N log-uniform in [1024, 2097152], theta U[0.5, 0.8],
-    10-200 KDK steps of dt 1e-3, eps 0.01) through bh_submit / bh_wait, with
-    continuous batching under a 160 GB HBM budget.  Particles of a request are
-    a seeded random subset of a pre-drawn 2^21-particle Plummer sphere or
-    uniform cube, masses 1/N (a random subset of independent draws is itself
-    an independent draw)."""
+def serve_pools():
+    import synth
+    return {"plummer": synth.plummer(1 << 21, 51), "uniform": synth.uniform_cube(1 << 21, 52)}
+
+
+def serve_stream(B, rate_hz, seconds, seed, pools):
+    """Poisson request stream through bh_submit / bh_wait with continuous
+    batching under a 160 GB HBM budget; each request a Plummer or uniform system
+    of N log-uniform in [1024, 2097152], theta U[0.5, 0.8], 10-200 KDK steps of
+    dt 1e-3, eps 0.01.  Particles of a request are a seeded random subset of a
+    pre-drawn 2^21-particle Plummer sphere or uniform cube, masses 1/N (a random
+    subset of independent draws is itself an independent draw)."""
     import numpy as np
     import synth
-    reqs = synth.request_stream(rate_hz=200.0, duration_s=args.serve_seconds, seed=5)
-    pools = {"plummer": synth.plummer(1 << 21, 51), "uniform": synth.uniform_cube(1 << 21, 52)}
+    reqs = synth.request_stream(rate_hz=rate_hz, duration_s=seconds, seed=seed)
     payload = []
     for r in reqs:
         rng = np.random.default_rng(r.seed)
@@ -510,15 +513,29 @@ def bench_served(args, B, torch):
     lat = np.array([x["done_s"] - x["submit_s"] for x in res])
     ps = sum(r.n * r.steps for r in reqs)
     span = max(x["done_s"] for x in res) - min(x["submit_s"] for x in res)
-    offered = ps / max(args.serve_seconds, 1e-9)
-    return {"workload": f"{len(reqs)} requests, Poisson 200/s over {args.serve_seconds} s, "
+    return {"workload": f"{len(reqs)} requests, Poisson {rate_hz:.3g}/s over {seconds} s, "
                         "N log-uniform [1024, 2097152], theta U[0.5,0.8], 10-200 steps dt 1e-3, "
-                        "Plummer/uniform 50/50, seed 5",
+                        f"Plummer/uniform 50/50, seed {seed}",
             "value": ps / span, "unit": UNIT, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
-            "offered_particle_steps_per_s": offered, "requests": len(reqs),
+            "offered_particle_steps_per_s": ps / max(seconds, 1e-9), "requests": len(reqs),
             "peak_resident_systems": stats["peak_resident_systems"],
             "ticks": stats["ticks"], "busy_s": stats["busy_s"]}
+
+
+def bench_served(args, B, torch):
+    """The request stream of the served workload (200 requests/s), then the
+    same mix at half the throughput the first run measured, where latency is
+    service time rather than queueing."""
+    pools = serve_pools()
+    out = serve_stream(B, 200.0, args.serve_seconds, 5, pools)
+    if args.serve_light_seconds > 0:
+        per_request = out["offered_particle_steps_per_s"] / 200.0  # particle-steps per request
+        rate = 0.5 * out["value"] / max(per_request, 1.0)
+        light = serve_stream(B, rate, args.serve_light_seconds, 6, pools)
+        light["load"] = "offered load = 0.5 x the throughput measured at 200 requests/s"
+        out["half_load"] = light
+    return out
 
 
 def main():
@@ -544,6 +561,8 @@ def main():
     ap.add_argument("--forest-systems", type=int, default=512)
     ap.add_argument("--forest-steps", type=int, default=100)
     ap.add_argument("--plain-steps", type=int, default=10)
+    ap.add_argument("--serve-light-seconds", type=float, default=8.0,
+                    help="seconds of arrivals for the half-load served run (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=0.5,
                     help="length of the Poisson arrival window (200 requests/s)")
     ap.add_argument("--workload", default="uniform1m", choices=sorted(WORKLOADS))

@@ -157,7 +157,10 @@ int bh_destroy(bh_system *s);
 /* Replaces the state (n x 4 each).  vel NULL keeps the current velocities.
  * acc, if not NULL, is taken as the acceleration of the new positions (as
  * returned by bh_get_state), so the next bh_step needs no extra force
- * evaluation; if NULL the stored acceleration is invalidated. */
+ * evaluation; if NULL the stored acceleration is invalidated.  The new state
+ * is checked on the device first (finite coordinates and velocities,
+ * positive masses): BH_ERR_INVALID leaves the old state in place.  On return
+ * the caller's buffers have been read and may be reused. */
 int bh_set_state(bh_system *s, const float *pos_mass, const float *vel, const float *acc,
                  unsigned flags);
 

@@ -978,25 +978,30 @@ int bh_set_state(bh_system *s, const float *pos_mass, const float *vel, const fl
     TRY(s->f.begin_call());
     Forest &f = s->f;
     SysState &S = *f.systems[0];
-    // stage into the step-backup arrays and check there, so a rejected
-    // state leaves the system as it was
+    // stage into the step-backup arrays (and the accelerations into the
+    // sorted-position scratch, which the next build rewrites before any use)
+    // and check there, so a rejected state leaves the system as it was
     TRY(upload4(S.bpos(), pos_mass, S.n, flags, f.st));
     if (vel) TRY(upload4(S.bvel(), vel, S.n, flags, f.st));
+    float4 *acc_stage = f.spos.as<float4>();
+    if (acc) TRY(upload4(acc_stage, acc, S.n, flags, f.st));
     TRY(f.clear_status());
     launch_validate_arrays(S.bpos(), vel ? S.bvel() : nullptr, (int)S.n, f.small(), f.nsm, f.st);
     f.launches += 1;
+    // the one synchronisation: every caller buffer has been read once it returns
     TRY(f.read_small());
     if (f.h_small->status == ST_BAD_INPUT) {
         f.clear_status();
         return fail(BH_ERR_INVALID, "non-finite coordinate or non-positive mass");
     }
+    // device-side copies only: later calls on the stream are ordered after them
     const size_t nb = (size_t)S.n * sizeof(float4);
     CKR(cudaMemcpyAsync(S.pos(), S.bpos(), nb, cudaMemcpyDeviceToDevice, f.st));
     if (vel) CKR(cudaMemcpyAsync(S.vel(), S.bvel(), nb, cudaMemcpyDeviceToDevice, f.st));
-    if (acc) TRY(upload4(S.acc(), acc, S.n, flags, f.st));
+    if (acc) CKR(cudaMemcpyAsync(S.acc(), acc_stage, nb, cudaMemcpyDeviceToDevice, f.st));
     s->f.acc_valid = acc != nullptr;
     s->f.tree_valid = false;
-    return s->f.sync();
+    return BH_OK;
 }
 
 int bh_build_tree(bh_system *s)

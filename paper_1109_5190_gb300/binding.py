@@ -167,9 +167,15 @@ def _stream(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
-def params(G=1.0, eps=0.01, theta=0.5, flags=0) -> bh_params:
+def bh_params_default() -> bh_params:
     p = bh_params()
     _check(lib.bh_params_default(C.byref(p)))
+    return p
+
+
+def params(G=1.0, eps=0.01, theta=0.5, flags=0) -> bh_params:
+    """bh_params_default() with G, eps, theta and flags set."""
+    p = bh_params_default()
     p.G, p.eps, p.theta, p.flags = float(G), float(eps), float(theta), int(flags)
     return p
 

@@ -46,6 +46,9 @@ def test_binding_wraps_every_symbol(lib):
     from paper_1109_5190_gb300 import binding
     missing = [n for n in declared_functions() if n not in binding._SIGS]
     assert not missing, missing
+    # and offers a Python function of the same name for each
+    unnamed = [n for n in declared_functions() if not callable(getattr(binding, n, None))]
+    assert not unnamed, unnamed
 
 
 def test_host_side_argument_errors(lib):

@@ -127,8 +127,15 @@ for _name, (_args, _res) in _SIGS.items():
     _f.restype = _res
 
 
-def last_error() -> str:
+def bh_last_error() -> str:
     return lib.bh_last_error().decode()
+
+
+def bh_version() -> str:
+    return lib.bh_version().decode()
+
+
+last_error = bh_last_error
 
 
 def _check(rc: int) -> int:

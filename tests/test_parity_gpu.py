@@ -369,6 +369,38 @@ def test_server_results_same_alone_and_in_mix():
         assert np.array_equal(out["pos_mass"], x) and np.array_equal(out["acc"], a)
 
 
+def test_server_admission_by_budget_and_slots():
+    # a request larger than the HBM budget is refused at submit; the others
+    # are admitted first come, first served, never more than the slots, and
+    # each result equals the same request solved alone
+    srv = B.bh_server_create(16 << 20, 2)
+    try:
+        big, bv = synth.plummer(100000, 31)
+        with pytest.raises(B.BHError) as e:
+            B.bh_submit(srv, big, bv, 1.0, 0.01, 0.5, 1e-3, 2)
+        assert e.value.code == B.BH_ERR_BUDGET
+        reqs = [synth.plummer(8000 + 500 * k, 40 + k) for k in range(5)]
+        tickets = [B.bh_submit(srv, pm, v, 1.0, 0.01, 0.5, 1e-3, 3) for pm, v in reqs]
+        res = [B.bh_wait(srv, t, len(pm), 120.0) for t, (pm, v) in zip(tickets, reqs)]
+        st = B.bh_server_stats_get(srv)
+        assert st["rejected"] == 1 and st["completed"] == 5
+        assert st["peak_resident_systems"] <= 2
+        assert st["peak_resident_bytes"] <= 16 << 20
+        admits = [r["admit_s"] for r in res]
+        assert admits == sorted(admits)
+    finally:
+        B.bh_server_destroy(srv)
+    for (pm, v), out in zip(reqs, res):
+        h = make(pm, v, eps=0.01, theta=0.5)
+        try:
+            B.bh_step(h, 3, 1e-3)
+            x = np.zeros_like(pm); a = np.zeros_like(pm)
+            B.bh_get_state(h, x, None, a)
+        finally:
+            B.bh_destroy(h)
+        assert np.array_equal(out["pos_mass"], x) and np.array_equal(out["acc"], a)
+
+
 def test_uniform_cube_million_step0_all_particles():
     # uniform cube N = 2^20, eps = 0.005, theta in {0.5, 0.7}, 20 KDK steps of
     # dt = 5e-4: every particle against the oracle at step 0, then a seeded

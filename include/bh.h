@@ -112,11 +112,17 @@ typedef struct bh_node {
  *                   (ppl 1): the warp walks the union of the top levels
  *                   (level <= clamp(floor(log8 n) - 3, 2, 5)), then every lane
  *                   walks the subtrees below them that it opened on its own.
- * Accelerations are bit-identical for every shape with group >= 1.  The split
+ *                   BH_GROUP_LIST (64) = interaction lists (ppl 1): the warp
+ *                   walks the union of its tile's traversals into a list of
+ *                   (node, lanes that take it), then evaluates the list.
+ * Accelerations are bit-identical for every shape with group >= 1 (the
+ * interaction lists included).  The split
  * walk sums the same terms in another order, fixed by each particle's tile (32
  * consecutive sorted particles of its system), so its results are
  * bit-identical among split shapes, alone or in a forest, and differ from the
  * others only by rounding; interaction counts are the same for every shape. */
+#define BH_GROUP_LIST 64
+
 typedef struct bh_tuning {
     int ppl;
     int warps_per_block;

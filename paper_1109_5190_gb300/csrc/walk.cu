@@ -557,6 +557,154 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
     }
 }
 
+// ------------------------------------------------------ interaction lists
+//
+// The paper's two-phase form (a flattened tree walked into interaction
+// lists, then the lists evaluated), per tile of 32 particles and exact per
+// particle:
+//   1. the warp walks the union of its particles' traversals (vote on the
+//      smallest next index, one broadcast node load per step, every lane
+//      decides for itself) and appends each node that some lane takes --
+//      accepted cell, leaf or depth-cap bucket -- with the mask of the lanes
+//      that take it, to a list in shared memory;
+//   2. the warp evaluates the list in order: one broadcast load per entry,
+//      and every lane whose bit is set adds the term, with no decisions left.
+// A full list is evaluated before the walk goes on.  Every particle adds its
+// own terms in depth-first order, as in k_walk, so results are bit-identical
+// to every other shape with a vote group.
+constexpr int kListCap = 128;      // entries per warp
+constexpr int kListMaxWarps = 16;  // warps per block
+
+template <bool KAHAN, bool POT, bool COUNT>
+__global__ void __launch_bounds__(512, 3) k_walk_list(WalkArgs a)
+{
+    __shared__ uint2 s_list[kListMaxWarps][kListCap];  // (node, lane mask)
+    __shared__ unsigned s_next;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    Small *sm = a.small;
+    if (sm->status) return;
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    const int per_block = (int)(((long long)a.ntiles * a.static_share / 100) / gridDim.x);
+    const int nstatic = per_block * (int)gridDim.x;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) {
+            const int k = (int)atomicAdd(&s_next, 1u);
+            t = k < per_block ? range_of_block(a.nsm) * per_block + k
+                              : nstatic + (int)atomicAdd(&sm->queue, 1u);
+        }
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= a.ntiles) break;
+        const Tile tl = a.tiles[t];
+        const int sysid = tl.sys;
+        int root, nend;
+        float eps2;
+        {
+            const SysStatic &S = a.sys[sysid];
+            root = (int)a.noff[S.start];
+            nend = (int)a.noff[S.start + S.n];
+            eps2 = S.eps2;
+        }
+        const int myj = tl.start + lane;
+        const bool live = lane < tl.count;
+        float px = 0.f, py = 0.f, pz = 0.f;
+        if (live) {
+            const float4 P = a.spos[myj];
+            px = P.x; py = P.y; pz = P.z;
+        }
+        float ax = 0.f, ay = 0.f, az = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pp = 0.f, cp = 0.f;
+        unsigned cnt = 0, iters = 0, vis = 0;
+        int nxt = live ? root : nend;
+        bool done = false;
+        while (!done) {
+            // ---- phase 1: walk the union, list what the lanes take
+            int n = 0;  // warp-uniform
+            while (n < kListCap) {
+                const int cur = (int)__reduce_min_sync(FULL, (unsigned)nxt);
+                if (cur >= nend) {
+                    done = true;
+                    break;
+                }
+                if (COUNT) ++iters;
+                float4 A;
+                uint4 B;
+                load_node(a.nodeW + cur, A, B);
+                const int skip = wn_skip(B);  // > cur, checked by the topology pass
+                const float crit = wn_crit(B);
+                bool take = false;
+                if (nxt == cur) {
+                    if (COUNT) ++vis;
+                    const float band = crit * kTieBand;
+                    const float lscale = __int_as_float(B.w & 0x7f800000u);
+                    const float dx = fmaf((float)(short)(B.z & 0xffffu), lscale, A.x - px);
+                    const float dy = fmaf((float)(short)(B.z >> 16), lscale, A.y - py);
+                    const float dz = fmaf((float)(short)(B.w & 0xffffu), lscale, A.z - pz);
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    const float diff = d2 - crit;
+                    bool acc = diff > 0.f;
+                    if (fabsf(diff) < band)
+                        acc = accept_fp64(a.nodeD, a.nodeR, a.sys, a.dyn, sysid, cur, px, py, pz);
+                    take = acc || crit == kBucketCrit;
+                    nxt = take ? skip : cur + 1;
+                }
+                const unsigned m = __ballot_sync(FULL, take);
+                if (m) {
+                    if (lane == 0) s_list[warp][n] = make_uint2((unsigned)cur, m);
+                    ++n;
+                }
+            }
+            __syncwarp();
+            // ---- phase 2: evaluate the list, entry by entry in walk order
+            for (int e = 0; e < n; ++e) {
+                const uint2 E = s_list[warp][e];
+                if (COUNT) ++iters;
+                float4 A;
+                uint4 B;
+                load_node(a.nodeW + E.x, A, B);
+                if (!((E.y >> lane) & 1u)) continue;
+                const float crit = wn_crit(B);
+                if (crit == kBucketCrit) {
+                    bucket_sum<KAHAN, POT, COUNT>(a.nodeR, a.spos, (int)E.x, px, py, pz, myj, eps2,
+                                                  ax, ay, az, cx, cy, cz, pp, cp, cnt);
+                    continue;
+                }
+                const float lscale = __int_as_float(B.w & 0x7f800000u);
+                const float dx = fmaf((float)(short)(B.z & 0xffffu), lscale, A.x - px);
+                const float dy = fmaf((float)(short)(B.z >> 16), lscale, A.y - py);
+                const float dz = fmaf((float)(short)(B.w & 0xffffu), lscale, A.z - pz);
+                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[E.x].x) == myj;
+                interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az, cx, cy,
+                                            cz, pp, cp, cnt);
+            }
+            __syncwarp();
+        }
+
+        if (COUNT) {
+            unsigned long long ci = live ? cnt : 0u, cv = live ? vis : 0u;
+            for (int o = 16; o > 0; o >>= 1) {
+                ci += __shfl_down_sync(FULL, ci, o);
+                cv += __shfl_down_sync(FULL, cv, o);
+            }
+            if (lane == 0) {
+                atomicAdd(&sm->wstats[0], ci);
+                atomicAdd(&sm->wstats[1], (unsigned long long)iters);
+                atomicAdd(&sm->wstats[2], cv);
+            }
+        }
+        if (live) {
+            const uint32_t v = a.sid[myj];
+            const SysStatic &S = a.sys[sysid];
+            const float G = S.G;
+            if (COUNT) a.counts[v] = cnt;
+            else S.acc[(int)v - S.start] = make_float4(G * ax, G * ay, G * az, POT ? -G * pp : 0.f);
+        }
+        __syncwarp();
+    }
+}
+
 // Blocks of `warps` warps that fit on one SM, queried once per variant and
 // block size (never during stream capture: callers query before capturing).
 template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT>
@@ -617,6 +765,44 @@ int launch_split(const WalkArgs *a, const WalkShape &sh, int nsm, cudaStream_t s
     return occ;
 }
 
+template <bool KAHAN, bool POT, bool COUNT>
+int occupancy_list(int warps)
+{
+    static int cache[33] = {0};
+    if (warps < 1 || warps > kListMaxWarps) return 0;
+    if (cache[warps] == 0) {
+        auto *fn = k_walk_list<KAHAN, POT, COUNT>;
+        cudaFuncAttributes fa{};
+        int occ = 0;
+        if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess) {
+            const int regs = fa.numRegs > 0 ? fa.numRegs : 64;
+            const int per_sm = 65536 / (regs * warps * 32);
+            const int want = per_sm < 1 ? 1 : (per_sm > 64 / warps ? 64 / warps : per_sm);
+            const size_t need = (size_t)want * (fa.sharedSizeBytes + 1024) * 100;
+            const int pct = (int)((need + 228 * 1024 - 1) / (228 * 1024));
+            cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 pct > 100 ? 100 : pct);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, warps * 32, 0) != cudaSuccess)
+                occ = 0;
+        }
+        cache[warps] = occ > 0 ? occ : -1;
+    }
+    return cache[warps] > 0 ? cache[warps] : 0;
+}
+
+template <bool KAHAN, bool POT, bool COUNT>
+int launch_list(const WalkArgs *a, const WalkShape &sh, int nsm, cudaStream_t st)
+{
+    if (sh.ppl != 1) return 0;
+    const int occ = occupancy_list<KAHAN, POT, COUNT>(sh.warps);
+    if (occ <= 0) return 0;
+    if (a) {
+        const int bps = sh.blocks_per_sm > 0 ? sh.blocks_per_sm : occ;
+        k_walk_list<KAHAN, POT, COUNT><<<nsm * bps, sh.warps * 32, 0, st>>>(*a);
+    }
+    return occ;
+}
+
 template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT>
 void launch_one(const WalkArgs &a, const WalkShape &sh, int nsm, cudaStream_t st)
 {
@@ -658,6 +844,13 @@ struct Variants {
     static int run(bool kahan, bool pot, const WalkArgs *a, const WalkShape &sh, int nsm,
                    cudaStream_t st)
     {
+        if (sh.group == BH_GROUP_LIST) {  // interaction lists
+            if (COUNT) return launch_list<true, false, true>(a, sh, nsm, st);
+            if (kahan && pot) return launch_list<true, true, false>(a, sh, nsm, st);
+            if (kahan) return launch_list<true, false, false>(a, sh, nsm, st);
+            if (pot) return launch_list<false, true, false>(a, sh, nsm, st);
+            return launch_list<false, false, false>(a, sh, nsm, st);
+        }
         if (sh.group == 0) {  // split walk
             if (COUNT) return launch_split<true, false, true>(a, sh, nsm, st);
             if (kahan && pot) return launch_split<true, true, false>(a, sh, nsm, st);

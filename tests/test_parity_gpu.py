@@ -155,7 +155,7 @@ def test_kepler_two_body_closed_form():
         B.bh_destroy(h)
 
 
-@pytest.mark.parametrize("group", [1, 32, 0])
+@pytest.mark.parametrize("group", [1, 32, 0, 64])
 def test_potential_and_diagnostics(group):
     pm, vel = synth.plummer(4096, 14)
     h = make(pm, vel, eps=0.01, theta=0.5, flags=B.BH_POTENTIAL)
@@ -227,7 +227,7 @@ def test_launch_shape_does_not_change_results():
     try:
         refs, counts = {}, {}
         for group, ppl in ((1, 1), (1, 2), (1, 4), (2, 1), (4, 1), (4, 2), (8, 1), (8, 2), (32, 1),
-                           (32, 2), (32, 4), (0, 1)):
+                           (32, 2), (32, 4), (B.BH_GROUP_LIST, 1), (0, 1)):
             fam = "split" if group == 0 else "dfs"
             for w in (4, 8, 16):
                 for share in ((0, 75) if ppl == 1 else (75,)):

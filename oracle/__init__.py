@@ -59,7 +59,7 @@ def _load():
         L.oracle_tree_cube.argtypes = [P, P, P]
         L.oracle_tree_export.argtypes = [P, P, P, P, P, P, P, P]
         L.oracle_tree_order.argtypes = [P, P, P]
-        L.oracle_accel.argtypes = [P, dbl, dbl, dbl, i64, P, P, P, P, i32]
+        L.oracle_accel.argtypes = [P, dbl, dbl, dbl, i64, P, P, P, P, i32, i32]
         L.oracle_accel.restype = i32
         L.oracle_direct.argtypes = [i64, P, dbl, dbl, i64, P, P, P, i32]
         L.oracle_direct.restype = i32
@@ -146,8 +146,9 @@ class Tree:
         return o, k
 
     def accel(self, theta: float, eps: float, G: float = 1.0, targets=None,
-              nthreads: int = 0):
-        """(acc (nt,3), pot (nt,), count (nt,)) for the target input indices."""
+              nthreads: int = 0, open_inside: bool = False):
+        """(acc (nt,3), pot (nt,), count (nt,)) for the target input indices.
+        open_inside: never accept a cell that contains the particle."""
         if targets is None:
             nt, tp = self.n, None
         else:
@@ -157,7 +158,7 @@ class Tree:
         pot = np.zeros(nt, np.float64)
         cnt = np.zeros(nt, np.int64)
         _load().oracle_accel(self._h, G, eps, theta, nt, _ptr(tp), _ptr(acc), _ptr(pot),
-                             _ptr(cnt), int(nthreads))
+                             _ptr(cnt), int(nthreads), int(bool(open_inside)))
         return acc, pot, cnt
 
 

@@ -26,7 +26,8 @@
  *   - opening test: a cell of side s = side / 2^level at distance d from the
  *     particle (d measured to the cell's centre of mass) is accepted as one
  *     body iff s^2 < theta^2 d^2 (strict); theta = 0 never accepts, which is
- *     direct summation; leaves are always taken particle by particle;
+ *     direct summation; leaves are always taken particle by particle
+ *     (optionally, a cell that contains the particle is always opened);
  *   - keys: the bounding cube is anchored at the per-axis minimum of the FP32
  *     positions with side = the largest FP32 extent (1 if that is below 1e-30);
  *     each coordinate is quantised to 21 bits as
@@ -373,6 +374,7 @@ typedef struct {
     const otree *t;
     double G, eps2, theta2;
     int64_t self;
+    int open_inside;  /* never accept a cell that contains the particle */
     double xi[3];
     nsum a[3], phi;
     int64_t count;
@@ -407,7 +409,9 @@ static void walk(walker *w, int32_t ni)
     double dx = d->com[0] - w->xi[0], dy = d->com[1] - w->xi[1], dz = d->com[2] - w->xi[2];
     double d2 = dx * dx + dy * dy + dz * dz;
     double s = ldexp((double)t->side, -d->level);
-    if (s * s < w->theta2 * d2) {
+    /* the cell holds the particle iff its key starts with the cell's prefix */
+    int inside = (t->keys[w->self] >> (3 * (21 - d->level))) == d->prefix;
+    if (s * s < w->theta2 * d2 && !(w->open_inside && inside)) {
         term(w, d->m, d->com, 0);
         return;
     }
@@ -416,10 +420,13 @@ static void walk(walker *w, int32_t ni)
 }
 
 /* Accelerations (and potential, interaction count) of nt target particles
- * (input indices; NULL = all n) through the tree.  acc is nt * 3. */
+ * (input indices; NULL = all n) through the tree.  acc is nt * 3.
+ * open_inside != 0: the alternative opening rule that never accepts a cell
+ * containing the particle itself (the pure test can, for theta > 1/sqrt(3):
+ * the particle's own mass then enters an approximated cell). */
 int oracle_accel(const otree *t, double G, double eps, double theta, int64_t nt,
                  const int64_t *targets, double *acc, double *pot, int64_t *count,
-                 int nthreads)
+                 int nthreads, int open_inside)
 {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -434,6 +441,7 @@ int oracle_accel(const otree *t, double G, double eps, double theta, int64_t nt,
         w.eps2 = eps * eps;
         w.theta2 = theta * theta;
         w.self = i;
+        w.open_inside = open_inside;
         for (int a = 0; a < 3; ++a) w.xi[a] = t->x[4 * i + a];
         walk(&w, t->dfs[0]);
         for (int a = 0; a < 3; ++a) acc[3 * k + a] = G * nsum_get(&w.a[a]);
@@ -482,7 +490,7 @@ static int accel_all(int64_t n, const double *pm, double G, double eps, double t
 {
     otree *t = oracle_tree_build(n, pm);
     if (!t) return -1;
-    oracle_accel(t, G, eps, theta, n, NULL, acc, pot, NULL, nthreads);
+    oracle_accel(t, G, eps, theta, n, NULL, acc, pot, NULL, nthreads, 0);
     oracle_tree_free(t);
     return 0;
 }

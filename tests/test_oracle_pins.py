@@ -244,13 +244,14 @@ def test_error_decreases_as_theta_decreases(oracle_lib):
     assert errs[-1] < 1e-4
 
 
-def _frontier_accel(pm, theta, eps, lo_side):
+def _frontier_accel(pm, theta, eps, lo_side, open_inside=False):
     """The Barnes-Hut sum from its set definition, without recursion: particle
     i uses every node whose proper ancestors all fail the opening test s^2 <
     theta^2 d^2 for i while the node itself passes it, is a one-particle leaf,
     or is a depth-cap bucket (then each member particle).  Nodes by brute-force
     enumeration; centres of mass as direct sums over member particles."""
     nodes, order = _brute_force_nodes(pm)
+    keys_sorted = oracle.keys(pm)[order]
     x = pm[order, :3]
     m = pm[order, 3]
     side = float(lo_side[1])
@@ -263,9 +264,13 @@ def _frontier_accel(pm, theta, eps, lo_side):
     for i in range(n):
         xi = x[i]
 
+        key_i = int(keys_sorted[i])
+
         def opens(lvl, pre, cnt):
             if cnt == 1 or lvl == 21:
                 return False
+            if open_inside and (key_i >> (3 * (21 - lvl))) == pre:
+                return True
             M, c = com[(lvl, pre)]
             s = side * 2.0 ** -lvl
             return not (s * s < theta * theta * float(((c - xi) ** 2).sum()))
@@ -293,10 +298,11 @@ def _frontier_accel(pm, theta, eps, lo_side):
     return out_a, out_p, out_c
 
 
+@pytest.mark.parametrize("open_inside", [False, True])
 @pytest.mark.parametrize("kind,n,seed", [("gauss", 40, 11), ("clustered", 60, 12),
                                          ("planar", 50, 13), ("dups", 30, 14)])
 @pytest.mark.parametrize("theta", [0.3, 0.5, 0.7, 1.0])
-def test_walk_equals_set_definition(oracle_lib, kind, n, seed, theta):
+def test_walk_equals_set_definition(oracle_lib, kind, n, seed, theta, open_inside):
     # theta > 0: the recursive walk against the set definition of the sum it
     # computes, on inputs small enough to enumerate every node and ancestor
     if kind == "dups":
@@ -309,9 +315,9 @@ def test_walk_equals_set_definition(oracle_lib, kind, n, seed, theta):
     pm[:, 3] *= np.linspace(0.5, 1.5, n)  # unequal masses: a centroid is not the COM
     eps = 0.01
     T = oracle.Tree(pm)
-    a, p, c = T.accel(theta, eps)
+    a, p, c = T.accel(theta, eps, open_inside=open_inside)
     lo, side = T.cube()
-    wa, wp, wc = _frontier_accel(pm, theta, eps, (lo, side))
+    wa, wp, wc = _frontier_accel(pm, theta, eps, (lo, side), open_inside)
     assert np.array_equal(c, wc)
     scale = np.abs(wa).max()
     assert np.abs(a - wa).max() <= 1e-12 * scale
@@ -383,3 +389,18 @@ def test_plummer_generator_matches_model(oracle_lib):
     d = oracle.diagnostics(pm2, vel2, pot)
     assert abs(d[0] - 3 * math.pi / 64) < 0.1 * 3 * math.pi / 64
     assert abs(2 * d[0] + d[1]) < 0.1 * abs(d[1])
+
+
+def test_open_inside_changes_only_cells_holding_the_particle(oracle_lib):
+    # below theta = 1/sqrt(3) a cell holding the particle always fails the
+    # test (d <= sqrt(3) s), so the rule changes nothing; above it, it opens
+    # such cells and so adds interactions
+    pm, _ = synth.plummer(2000, 9)
+    T = oracle.Tree(pm)
+    for theta in (0.3, 0.5, 0.57):
+        a0, p0, c0 = T.accel(theta, 0.01)
+        a1, p1, c1 = T.accel(theta, 0.01, open_inside=True)
+        assert np.array_equal(c0, c1) and np.array_equal(a0, a1)
+    a0, _, c0 = T.accel(0.9, 0.01)
+    a1, _, c1 = T.accel(0.9, 0.01, open_inside=True)
+    assert np.all(c1 >= c0) and np.count_nonzero(c1 > c0) > 0

@@ -63,6 +63,10 @@ extern "C" {
 #define BH_DEVICE_PTRS  0x1u  /* pointer arguments are device pointers */
 #define BH_POTENTIAL    0x2u  /* the walk also accumulates phi (needed for PE) */
 #define BH_NO_KAHAN     0x4u  /* plain FP32 force sums instead of Kahan sums */
+#define BH_OPEN_INSIDE  0x8u  /* alternative opening rule: a cell that contains
+                                 the particle is always opened (the pure test of
+                                 Section III can accept it for theta > 1/sqrt(3));
+                                 the walk then runs one particle per lane */
 
 #define BH_MAX_DEPTH 21       /* levels below the root; fixed by the key width */
 

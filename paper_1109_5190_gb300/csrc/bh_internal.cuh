@@ -227,6 +227,7 @@ struct WalkShape {
     int warps;
     int blocks_per_sm;
     int group;
+    bool open_inside;  // BH_OPEN_INSIDE: one particle per lane, group 1
 };
 
 // kahan / potential / counting variants; returns number of kernel launches

@@ -459,10 +459,14 @@ struct Forest {
         return a;
     }
 
+    // BH_OPEN_INSIDE fixes the shape to one particle per lane
     WalkShape shape() const
     {
-        return WalkShape{tune.ppl, tune.warps_per_block, tune.blocks_per_sm, tune.group};
+        if (open_inside())
+            return WalkShape{1, tune.warps_per_block, tune.blocks_per_sm, 1, true};
+        return WalkShape{tune.ppl, tune.warps_per_block, tune.blocks_per_sm, tune.group, false};
     }
+    bool open_inside() const { return (flags & BH_OPEN_INSIDE) != 0; }
     bool kahan() const { return !(flags & BH_NO_KAHAN); }
     bool pot() const { return (flags & BH_POTENTIAL) != 0; }
 
@@ -719,7 +723,8 @@ struct Forest {
             for (int w : warps) {
                 for (int share : shares) {
                     bh_tuning t{p, w, 0, g, share};
-                    WalkShape sh{p, w, 0, g};
+                    if (open_inside() && (g != 1 || p != 1)) continue;
+                    WalkShape sh{p, w, 0, g, open_inside()};
                     if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0) continue;
                     tune = t;  // walk_args reads the static share from tune
                     float ms_best = 1e30f;
@@ -766,7 +771,10 @@ struct Forest {
             return fail(BH_ERR_INVALID, "bad tuning (group 1 or 32 with ppl 1/2/4, group 4/8 with "
                                         "ppl 1/2, group 2, 0 or BH_GROUP_LIST with ppl 1; warps "
                                         "1..16; static_share 0..90; blocks_per_sm >= 0)");
-        WalkShape sh{t->ppl, t->warps_per_block, t->blocks_per_sm, t->group};
+        // the shape as it would be launched (BH_OPEN_INSIDE: one particle per lane)
+        const WalkShape sh = open_inside()
+                                 ? WalkShape{1, t->warps_per_block, t->blocks_per_sm, 1, true}
+                                 : WalkShape{t->ppl, t->warps_per_block, t->blocks_per_sm, t->group, false};
         if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0)
             return fail(BH_ERR_INVALID, "walk shape does not fit on an SM");
         tune = *t;
@@ -792,7 +800,7 @@ struct Forest {
         TRY(ensure_tiles(1));
         TRY(clear_status());
         reset_step_counters();
-        WalkShape sh{1, 8, 0, tune.group};
+        WalkShape sh{1, 8, 0, open_inside() ? 1 : tune.group, open_inside()};
         CKR(cudaMemsetAsync(small()->wstats, 0, sizeof(small()->wstats), st));
         launch_walk(walk_args(1, d_counts.as<uint32_t>()), sh, true, false, true, nsm, st);
         launches += 1;
@@ -921,7 +929,8 @@ static int check_bh_params(const bh_params *p)
     TRY(check_params(p->G, p->eps, p->theta));
     if (p->max_depth != BH_MAX_DEPTH) return fail(BH_ERR_INVALID, "max_depth must be 21");
     if (p->leaf_cap != 1) return fail(BH_ERR_INVALID, "leaf_cap must be 1");
-    if (p->flags & ~(BH_POTENTIAL | BH_NO_KAHAN)) return fail(BH_ERR_INVALID, "unknown params flags");
+    if (p->flags & ~(BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE))
+        return fail(BH_ERR_INVALID, "unknown params flags");
     return BH_OK;
 }
 
@@ -1127,7 +1136,8 @@ int bh_forest_create(bh_forest **out, int nsys, const bh_system_desc *d, void *s
     if (!out) return fail(BH_ERR_INVALID, "null out");
     *out = nullptr;
     if (nsys < 1 || !d) return fail(BH_ERR_INVALID, "need at least one system");
-    if (flags & ~(BH_DEVICE_PTRS | BH_POTENTIAL | BH_NO_KAHAN)) return fail(BH_ERR_INVALID, "unknown flags");
+    if (flags & ~(BH_DEVICE_PTRS | BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE))
+        return fail(BH_ERR_INVALID, "unknown flags");
     for (int s = 0; s < nsys; ++s) {
         if (d[s].n < 1 || !d[s].pos_mass) return fail(BH_ERR_INVALID, "system " + std::to_string(s) + ": n < 1 or null pos_mass");
         TRY(check_params(d[s].G, d[s].eps, d[s].theta));
@@ -1135,7 +1145,7 @@ int bh_forest_create(bh_forest **out, int nsys, const bh_system_desc *d, void *s
     std::unique_ptr<bh_forest> F(new (std::nothrow) bh_forest);
     if (!F) return fail(BH_ERR_OOM, "host allocation failed");
     Forest &f = F->f;
-    TRY(f.init(stream, flags & (BH_POTENTIAL | BH_NO_KAHAN)));
+    TRY(f.init(stream, flags & (BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE)));
     f.tune.static_share = nsys > 1 ? 0 : f.tune.static_share;  // uneven tiles: all dynamic
     TRY(f.begin_call());
     for (int s = 0; s < nsys; ++s) {
@@ -1449,7 +1459,8 @@ int bh_server_create(bh_server **out, size_t hbm_budget, int max_slots, void *st
     if (!out) return fail(BH_ERR_INVALID, "null out");
     *out = nullptr;
     if (max_slots < 1 || hbm_budget < (1u << 20)) return fail(BH_ERR_INVALID, "bad budget or slot count");
-    if (flags & ~(BH_POTENTIAL | BH_NO_KAHAN)) return fail(BH_ERR_INVALID, "unknown flags");
+    if (flags & ~(BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE))
+        return fail(BH_ERR_INVALID, "unknown flags");
     std::unique_ptr<bh_server> s(new (std::nothrow) bh_server);
     if (!s) return fail(BH_ERR_OOM, "host allocation failed");
     s->budget = hbm_budget;

@@ -180,7 +180,7 @@ __device__ __forceinline__ void bucket_sum(const int4 *__restrict__ nodeR,
 // order, so its sums -- and the results -- do not depend on the shape.
 // Register budget: a block of up to 512 threads, and enough blocks per SM
 // for 48 resident warps with one particle per lane.
-template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT>
+template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false>
 __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
 {
     static_assert(GROUP == 1 || GROUP == 2 || GROUP == 4 || GROUP == 8 || GROUP == 16 ||
@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
 
         float px[PPL], py[PPL], pz[PPL];
         int nxt[PPL], myj[PPL];
+        int leaf[PPL];  // OPEN: node index of the slot's own leaf (or bucket)
         float ax[PPL], ay[PPL], az[PPL], cx[PPL], cy[PPL], cz[PPL], pp[PPL], cp[PPL];
         unsigned cnt[PPL], vis[PPL];
         unsigned iters = 0;
@@ -228,10 +229,14 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
             myj[k] = tl.start + o;
             ax[k] = ay[k] = az[k] = cx[k] = cy[k] = cz[k] = pp[k] = cp[k] = 0.f;
             cnt[k] = vis[k] = 0;
+            leaf[k] = -1;
             if (o < tl.count) {
                 const float4 P = a.spos[myj[k]];
                 px[k] = P.x; py[k] = P.y; pz[k] = P.z;
                 nxt[k] = root;
+                // the last node written at or before a particle is its leaf or
+                // its bucket (particles inside a bucket start no nodes)
+                if (OPEN) leaf[k] = (int)a.noff[myj[k] + 1] - 1;
             } else {
                 px[k] = py[k] = pz[k] = 0.f;
                 nxt[k] = nend;
@@ -290,6 +295,9 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
                     if (fabsf(diff) < band)
                         acc = accept_fp64(a.nodeD, a.nodeR, a.sys, a.dyn, tl.sys, cur, px[k],
                                           py[k], pz[k]);
+                    // alternative rule: a cell holding the particle (its leaf lies in
+                    // the cell's subtree, cur < leaf < skip) is always opened
+                    if (OPEN && acc && crit >= 0.f && cur < leaf[k] && leaf[k] < skip) acc = false;
                     if (acc) {
                         // the potential leaves out the particle's own leaf
                         const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[cur].x) == myj[k];
@@ -707,18 +715,18 @@ __global__ void __launch_bounds__(512, 3) k_walk_list(WalkArgs a)
 
 // Blocks of `warps` warps that fit on one SM, queried once per variant and
 // block size (never during stream capture: callers query before capturing).
-template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT>
+template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false>
 int occupancy(int warps)
 {
     static int cache[33] = {0};
     if (warps < 1 || warps > 32) return 0;
     if (cache[warps] == 0) {
         // the walk uses no shared memory: give the SM's unified storage to L1
-        cudaFuncSetAttribute(k_walk<PPL, GROUP, KAHAN, POT, COUNT>,
+        cudaFuncSetAttribute(k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, 0);
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &occ, k_walk<PPL, GROUP, KAHAN, POT, COUNT>, warps * 32, 0) != cudaSuccess)
+                &occ, k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN>, warps * 32, 0) != cudaSuccess)
             occ = 0;
         cache[warps] = occ > 0 ? occ : -1;
     }
@@ -803,14 +811,41 @@ int launch_list(const WalkArgs *a, const WalkShape &sh, int nsm, cudaStream_t st
     return occ;
 }
 
-template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT>
+template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false>
 void launch_one(const WalkArgs &a, const WalkShape &sh, int nsm, cudaStream_t st)
 {
     const int threads = sh.warps * 32;
     int bps = sh.blocks_per_sm;
-    if (bps <= 0) bps = occupancy<PPL, GROUP, KAHAN, POT, COUNT>(sh.warps);
+    if (bps <= 0) bps = occupancy<PPL, GROUP, KAHAN, POT, COUNT, OPEN>(sh.warps);
     if (bps <= 0) bps = 1;
-    k_walk<PPL, GROUP, KAHAN, POT, COUNT><<<nsm * bps, threads, 0, st>>>(a);
+    k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN><<<nsm * bps, threads, 0, st>>>(a);
+}
+
+// The walk under the alternative opening rule (BH_OPEN_INSIDE): one particle
+// per lane, no vote.
+template <bool COUNT>
+int run_open(bool kahan, bool pot, const WalkArgs *a, const WalkShape &sh, int nsm,
+             cudaStream_t st)
+{
+    if (sh.ppl != 1 || sh.group != 1) return 0;
+    if (COUNT) {
+        if (a) launch_one<1, 1, true, false, true, true>(*a, sh, nsm, st);
+        return occupancy<1, 1, true, false, true, true>(sh.warps);
+    }
+    if (kahan && pot) {
+        if (a) launch_one<1, 1, true, true, false, true>(*a, sh, nsm, st);
+        return occupancy<1, 1, true, true, false, true>(sh.warps);
+    }
+    if (kahan) {
+        if (a) launch_one<1, 1, true, false, false, true>(*a, sh, nsm, st);
+        return occupancy<1, 1, true, false, false, true>(sh.warps);
+    }
+    if (pot) {
+        if (a) launch_one<1, 1, false, true, false, true>(*a, sh, nsm, st);
+        return occupancy<1, 1, false, true, false, true>(sh.warps);
+    }
+    if (a) launch_one<1, 1, false, false, false, true>(*a, sh, nsm, st);
+    return occupancy<1, 1, false, false, false, true>(sh.warps);
 }
 
 // Dispatch of the runtime shape onto the compiled variants.
@@ -844,6 +879,7 @@ struct Variants {
     static int run(bool kahan, bool pot, const WalkArgs *a, const WalkShape &sh, int nsm,
                    cudaStream_t st)
     {
+        if (sh.open_inside) return run_open<COUNT>(kahan, pot, a, sh, nsm, st);
         if (sh.group == BH_GROUP_LIST) {  // interaction lists
             if (COUNT) return launch_list<true, false, true>(a, sh, nsm, st);
             if (kahan && pot) return launch_list<true, true, false>(a, sh, nsm, st);
@@ -903,6 +939,7 @@ int walk_max_blocks_per_sm(const WalkShape &sh, bool kahan, bool pot)
 {
     WalkShape cs = sh;
     cs.ppl = 1;
+    if (cs.open_inside) cs.group = 1;
     Variants<true>::run(true, false, nullptr, cs, 0, nullptr);  // the counting variant too
     return Variants<false>::run(kahan, pot, nullptr, sh, 0, nullptr);
 }

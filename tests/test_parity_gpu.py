@@ -401,6 +401,66 @@ def test_server_admission_by_budget_and_slots():
         assert np.array_equal(out["pos_mass"], x) and np.array_equal(out["acc"], a)
 
 
+@pytest.mark.parametrize("kind,n,seed", [("plummer", 5000, 41), ("uniform", 6000, 42),
+                                         ("dups", 1000, 43)])
+@pytest.mark.parametrize("theta", [0.7, 1.0])
+def test_open_inside_rule_against_oracle(kind, n, seed, theta):
+    # BH_OPEN_INSIDE: a cell holding the particle is always opened; counts are
+    # exact and forces within tolerance of the oracle under the same rule
+    pm, vel = gen(kind, n, seed)
+    h = make(pm, vel, 0.01, theta, flags=B.BH_POTENTIAL | B.BH_OPEN_INSIDE)
+    try:
+        a = gpu_accel(h, n)
+        T = oracle.Tree(pm)
+        ref, pot, cnt = T.accel(theta, 0.01, open_inside=True)
+        assert_accel_close(a, ref, what=f"open-inside {kind} theta={theta}")
+        e = np.abs(a[:, 3] - pot) / np.abs(pot)
+        assert np.percentile(e, 99) <= 1e-5
+        gc, _ = B.bh_interaction_count(h, n)
+        assert np.array_equal(gc.astype(np.int64), cnt)
+        if theta >= 1.0 and kind == "plummer":
+            # the pure test accepts a cell holding the particle only when the
+            # particle and the cell's centre of mass sit far apart inside it:
+            # common in a Plummer sphere at theta = 1, rare at 0.7, and in a
+            # uniform cube the centres of mass stay too close to the cell centres
+            _, _, cnt_pure = T.accel(theta, 0.01)
+            assert np.any(cnt != cnt_pure)
+        B.bh_step(h, 2, 1e-3)  # the KDK steps run under the rule too
+        x = np.zeros_like(pm); a = np.zeros_like(pm)
+        B.bh_get_state(h, x, None, a)
+        ref, _, _ = oracle.Tree(x).accel(theta, 0.01, open_inside=True)
+        assert_accel_close(a, ref, what=f"open-inside {kind} theta={theta} step 2")
+    finally:
+        B.bh_destroy(h)
+
+
+def test_open_inside_rule_changes_nothing_below_its_threshold():
+    # theta < 1/sqrt(3): a cell holding the particle never passes the test,
+    # so the rule leaves every result bit-identical; in a forest as well
+    pm, vel = synth.plummer(8000, 44)
+    outs = []
+    for fl in (0, B.BH_OPEN_INSIDE):
+        h = make(pm, vel, 0.01, 0.5, flags=fl)
+        try:
+            outs.append(gpu_accel(h, 8000))
+        finally:
+            B.bh_destroy(h)
+    assert np.array_equal(outs[0], outs[1])
+    systems = synth.forest_systems(6, 256, 4000, seed=45, theta=0.5, eps=0.01)
+    descs = [dict(pos_mass=s.pos_mass, vel=s.vel, eps=s.eps, theta=0.9, dt=1e-3) for s in systems]
+    f = B.bh_forest_create(descs, flags=B.BH_OPEN_INSIDE)
+    try:
+        B.bh_forest_compute_accel(f)
+        for k, d in enumerate(descs):
+            n = len(d["pos_mass"])
+            af = np.zeros((n, 4), np.float32)
+            B.bh_forest_get_state(f, k, None, None, af)
+            ref, _, _ = oracle.Tree(d["pos_mass"]).accel(0.9, 0.01, open_inside=True)
+            assert_accel_close(af, ref, what=f"open-inside forest system {k}")
+    finally:
+        B.bh_forest_destroy(f)
+
+
 def test_uniform_cube_million_step0_all_particles():
     # uniform cube N = 2^20, eps = 0.005, theta in {0.5, 0.7}, 20 KDK steps of
     # dt = 5e-4: every particle against the oracle at step 0, then a seeded

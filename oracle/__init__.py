@@ -146,9 +146,10 @@ class Tree:
         return o, k
 
     def accel(self, theta: float, eps: float, G: float = 1.0, targets=None,
-              nthreads: int = 0, open_inside: bool = False):
+              nthreads: int = 0, open_inside: bool = False, quadrupole: bool = False):
         """(acc (nt,3), pot (nt,), count (nt,)) for the target input indices.
-        open_inside: never accept a cell that contains the particle."""
+        open_inside: never accept a cell that contains the particle;
+        quadrupole: accepted cells add their second-order term."""
         if targets is None:
             nt, tp = self.n, None
         else:
@@ -158,7 +159,8 @@ class Tree:
         pot = np.zeros(nt, np.float64)
         cnt = np.zeros(nt, np.int64)
         _load().oracle_accel(self._h, G, eps, theta, nt, _ptr(tp), _ptr(acc), _ptr(pot),
-                             _ptr(cnt), int(nthreads), int(bool(open_inside)))
+                             _ptr(cnt), int(nthreads),
+                             int(bool(open_inside)) | (2 if quadrupole else 0))
         return acc, pot, cnt
 
 

@@ -165,6 +165,7 @@ typedef struct {
     /* filled after insertion */
     int64_t first, count;  /* range in the canonical particle order */
     double m, com[3];
+    double I[6];           /* second moments about com: xx, yy, zz, xy, xz, yz */
 } onode;
 
 typedef struct otree {
@@ -178,6 +179,7 @@ typedef struct otree {
     int64_t *order;        /* canonical order -> input index */
     int64_t *dfs;          /* canonical node order -> storage index */
     int64_t ndfs;
+    int have_moments;      /* onode.I filled */
 } otree;
 
 static int32_t new_node(otree *t, int level, uint64_t prefix)
@@ -368,6 +370,33 @@ void oracle_tree_order(const otree *t, int64_t *order, uint64_t *keys)
     if (keys) memcpy(keys, t->keys, (size_t)t->n * sizeof(uint64_t));
 }
 
+/* Second moments of every cell about its centre of mass, by their definition
+ * I_ab = sum_j m_j (x_j - com)_a (x_j - com)_b over the member particles
+ * (used by the quadrupole term of the walk). */
+static void second_moments(otree *t)
+{
+    if (t->have_moments) return;
+    for (int64_t k = 0; k < t->ndfs; ++k) {
+        onode *d = &t->nodes[t->dfs[k]];
+        nsum I[6];
+        memset(I, 0, sizeof I);
+        for (int64_t q = d->first; q < d->first + d->count; ++q) {
+            int64_t p = t->order[q];
+            double m = t->x[4 * p + 3];
+            double r0 = t->x[4 * p] - d->com[0], r1 = t->x[4 * p + 1] - d->com[1],
+                   r2 = t->x[4 * p + 2] - d->com[2];
+            nsum_add(&I[0], m * r0 * r0);
+            nsum_add(&I[1], m * r1 * r1);
+            nsum_add(&I[2], m * r2 * r2);
+            nsum_add(&I[3], m * r0 * r1);
+            nsum_add(&I[4], m * r0 * r2);
+            nsum_add(&I[5], m * r1 * r2);
+        }
+        for (int a = 0; a < 6; ++a) d->I[a] = nsum_get(&I[a]);
+    }
+    t->have_moments = 1;
+}
+
 /* ------------------------------------------------------------------ walk */
 
 typedef struct {
@@ -375,6 +404,7 @@ typedef struct {
     double G, eps2, theta2;
     int64_t self;
     int open_inside;  /* never accept a cell that contains the particle */
+    int quad;         /* add each accepted cell's quadrupole term */
     double xi[3];
     nsum a[3], phi;
     int64_t count;
@@ -392,6 +422,34 @@ static void term(walker *w, double m, const double *xj, int is_self)
     nsum_add(&w->a[1], m * dy * inv3);
     nsum_add(&w->a[2], m * dz * inv3);
     if (!is_self) nsum_add(&w->phi, -m / r);
+}
+
+/* The second-order term of an accepted cell: the softened kernel
+ * g = 1/sqrt(|d|^2 + eps^2), d = com - x_i, expanded about the centre of mass
+ * to second order in the member offsets,
+ *   sum_j m_j g(d + r_j) ~ M g(d) + (1/2) I_ab d_a d_b g(d)   (sum_j m_j r_j = 0),
+ * with Hessian H_ab = 3 d_a d_b / s^5 - delta_ab / s^3, s^2 = |d|^2 + eps^2.
+ * Potential: -(1/2) I:H.  Acceleration: minus the gradient with respect to
+ * x_i, i.e. the d-gradient of (1/2) I:H:
+ *   -3 (I d) / s^5 + (15/2) (d.I.d) d / s^7 - (3/2) tr(I) d / s^5. */
+static void quad_term(walker *w, const onode *d)
+{
+    double dx = d->com[0] - w->xi[0], dy = d->com[1] - w->xi[1], dz = d->com[2] - w->xi[2];
+    double s2 = dx * dx + dy * dy + dz * dz + w->eps2;
+    if (s2 == 0.0) return;
+    double s = sqrt(s2);
+    double s3 = s2 * s, s5 = s3 * s2, s7 = s5 * s2;
+    const double *I = d->I;
+    double Id0 = I[0] * dx + I[3] * dy + I[4] * dz;
+    double Id1 = I[3] * dx + I[1] * dy + I[5] * dz;
+    double Id2 = I[4] * dx + I[5] * dy + I[2] * dz;
+    double dId = dx * Id0 + dy * Id1 + dz * Id2;
+    double tr = I[0] + I[1] + I[2];
+    double c = 7.5 * dId / s7 - 1.5 * tr / s5;
+    nsum_add(&w->a[0], -3.0 * Id0 / s5 + c * dx);
+    nsum_add(&w->a[1], -3.0 * Id1 / s5 + c * dy);
+    nsum_add(&w->a[2], -3.0 * Id2 / s5 + c * dz);
+    nsum_add(&w->phi, -0.5 * (3.0 * dId / s5 - tr / s3));
 }
 
 static void walk(walker *w, int32_t ni)
@@ -413,6 +471,7 @@ static void walk(walker *w, int32_t ni)
     int inside = (t->keys[w->self] >> (3 * (21 - d->level))) == d->prefix;
     if (s * s < w->theta2 * d2 && !(w->open_inside && inside)) {
         term(w, d->m, d->com, 0);
+        if (w->quad) quad_term(w, d);
         return;
     }
     for (int o = 0; o < 8; ++o)
@@ -421,13 +480,15 @@ static void walk(walker *w, int32_t ni)
 
 /* Accelerations (and potential, interaction count) of nt target particles
  * (input indices; NULL = all n) through the tree.  acc is nt * 3.
- * open_inside != 0: the alternative opening rule that never accepts a cell
+ * options bit 0: the alternative opening rule that never accepts a cell
  * containing the particle itself (the pure test can, for theta > 1/sqrt(3):
- * the particle's own mass then enters an approximated cell). */
-int oracle_accel(const otree *t, double G, double eps, double theta, int64_t nt,
+ * the particle's own mass then enters an approximated cell); bit 1: each
+ * accepted cell adds its quadrupole (second-moment) term to the monopole. */
+int oracle_accel(otree *t, double G, double eps, double theta, int64_t nt,
                  const int64_t *targets, double *acc, double *pot, int64_t *count,
-                 int nthreads, int open_inside)
+                 int nthreads, int options)
 {
+    if (options & 2) second_moments(t);
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 16)
@@ -441,7 +502,8 @@ int oracle_accel(const otree *t, double G, double eps, double theta, int64_t nt,
         w.eps2 = eps * eps;
         w.theta2 = theta * theta;
         w.self = i;
-        w.open_inside = open_inside;
+        w.open_inside = (options & 1) != 0;
+        w.quad = (options & 2) != 0;
         for (int a = 0; a < 3; ++a) w.xi[a] = t->x[4 * i + a];
         walk(&w, t->dfs[0]);
         for (int a = 0; a < 3; ++a) acc[3 * k + a] = G * nsum_get(&w.a[a]);
@@ -490,7 +552,7 @@ static int accel_all(int64_t n, const double *pm, double G, double eps, double t
 {
     otree *t = oracle_tree_build(n, pm);
     if (!t) return -1;
-    oracle_accel(t, G, eps, theta, n, NULL, acc, pot, NULL, nthreads, 0);
+    oracle_accel(t, G, eps, theta, n, NULL, acc, pot, NULL, nthreads, 0);  /* monopoles */
     oracle_tree_free(t);
     return 0;
 }

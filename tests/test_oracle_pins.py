@@ -404,3 +404,74 @@ def test_open_inside_changes_only_cells_holding_the_particle(oracle_lib):
     a0, _, c0 = T.accel(0.9, 0.01)
     a1, _, c1 = T.accel(0.9, 0.01, open_inside=True)
     assert np.all(c1 >= c0) and np.count_nonzero(c1 > c0) > 0
+
+
+def _cluster_and_probe(D, seed=3):
+    """A compact cluster of 12 unequal masses (radius ~0.05) at the origin and a
+    light probe particle at distance D along a fixed direction; with theta =
+    0.9 the probe accepts the cluster's cell as one body."""
+    rng = np.random.default_rng(seed)
+    pts = rng.normal(0.0, 0.02, size=(12, 3))
+    m = rng.uniform(0.5, 1.5, 12)
+    pm = np.zeros((13, 4))
+    pm[:12, :3] = pts
+    pm[:12, 3] = m
+    u = np.array([0.48, 0.6, 0.64])
+    pm[12, :3] = D * u / np.linalg.norm(u)
+    pm[12, 3] = 1e-9
+    return pm
+
+
+def test_quadrupole_force_is_minus_gradient_of_its_potential(oracle_lib):
+    # the acceleration and potential formulas of the quadrupole term are
+    # written separately; a central difference of the potential at the probe
+    # must reproduce the acceleration there (monopole and quadrupole together)
+    pm = _cluster_and_probe(2.0)
+    T = oracle.Tree(pm)
+    a, _, c = T.accel(0.9, 0.01, targets=[12], quadrupole=True)
+    a_mono, _, c_mono = T.accel(0.9, 0.01, targets=[12])
+    assert c[0] == c_mono[0] == 1  # the whole cluster is one accepted cell
+    assert np.linalg.norm(a - a_mono) > 1e-6 * np.linalg.norm(a)  # the term matters here
+    h = 1e-5
+    grad = np.zeros(3)
+    for k in range(3):
+        phis = []
+        for sgn in (1.0, -1.0):
+            q = pm.copy()
+            q[12, k] += sgn * h
+            _, phi, cc = oracle.Tree(q).accel(0.9, 0.01, targets=[12], quadrupole=True)
+            assert cc[0] == 1
+            phis.append(phi[0])
+        grad[k] = (phis[0] - phis[1]) / (2 * h)
+    np.testing.assert_allclose(a[0], -grad, rtol=1e-6)
+
+
+def test_quadrupole_error_falls_one_order_faster(oracle_lib):
+    # relative to the exact pull of the cluster, the monopole error falls as
+    # D^-2 and the error with the quadrupole term as D^-3 (the next term of the
+    # expansion); checked by log-log slopes over D = 2 .. 16
+    Ds = np.array([2.0, 4.0, 8.0, 16.0])
+    em, eq = [], []
+    for D in Ds:
+        pm = _cluster_and_probe(D)
+        ad, _ = oracle.direct(pm, 0.01, targets=[12])
+        T = oracle.Tree(pm)
+        a0, _, _ = T.accel(0.9, 0.01, targets=[12])
+        a1, _, _ = T.accel(0.9, 0.01, targets=[12], quadrupole=True)
+        n = np.linalg.norm(ad[0])
+        em.append(np.linalg.norm(a0[0] - ad[0]) / n)
+        eq.append(np.linalg.norm(a1[0] - ad[0]) / n)
+    sm = np.polyfit(np.log(Ds), np.log(em), 1)[0]
+    sq = np.polyfit(np.log(Ds), np.log(eq), 1)[0]
+    assert -2.3 < sm < -1.7, sm
+    assert sq < -2.7, sq
+    assert all(q < m for q, m in zip(eq, em))
+
+
+def test_quadrupole_keeps_the_accepted_set(oracle_lib):
+    pm, _ = synth.plummer(1500, 21)
+    T = oracle.Tree(pm)
+    for theta in (0.5, 0.8):
+        _, _, c0 = T.accel(theta, 0.01)
+        _, _, c1 = T.accel(theta, 0.01, quadrupole=True)
+        assert np.array_equal(c0, c1)

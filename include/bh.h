@@ -67,6 +67,10 @@ extern "C" {
                                  the particle is always opened (the pure test of
                                  Section III can accept it for theta > 1/sqrt(3));
                                  the walk then runs one particle per lane */
+#define BH_QUADRUPOLE   0x10u /* accepted cells add their quadrupole term
+                                 (second moments about the centre of mass,
+                                 softened kernel expanded to second order);
+                                 one particle per lane, Kahan sums required */
 
 #define BH_MAX_DEPTH 21       /* levels below the root; fixed by the key width */
 

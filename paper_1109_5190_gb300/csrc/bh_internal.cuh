@@ -172,6 +172,11 @@ struct BuildBufs {
     int4 *nodeR;
     double4_32a *nodeD;
     uint32_t *nlist;
+    // quadrupole mode only (else null): FP64 second moments about the centre
+    // of mass (xx, yy, zz, xy, xz, yz per node) and their FP32 copy for the
+    // walk, two float4 per node: (xx, yy, zz, xy), (xz, yz, 0, 0)
+    double *nodeI;
+    float4 *nodeQ;
     unsigned node_cap;
     Small *small;
     int n_total;
@@ -188,6 +193,7 @@ void prepare_sort_kernels();
 void launch_permute(const BuildBufs &b, cudaStream_t st);
 void launch_topology(const BuildBufs &b, cudaStream_t st);
 void launch_com(const BuildBufs &b, cudaStream_t st);
+void launch_root_moments(const BuildBufs &b, cudaStream_t st);  // quadrupole mode
 void launch_kick(const BuildBufs &b, cudaStream_t st);
 void launch_restore(const BuildBufs &b, cudaStream_t st);
 void launch_validate(const BuildBufs &b, cudaStream_t st);
@@ -203,6 +209,7 @@ void launch_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *partials,
 
 struct WalkArgs {
     const WNode *nodeW;
+    const float4 *nodeQ;  // quadrupole mode: 2 float4 per node (else null)
     const int4 *nodeR;
     const double4_32a *nodeD;
     const SysDyn *dyn;
@@ -228,6 +235,7 @@ struct WalkShape {
     int blocks_per_sm;
     int group;
     bool open_inside;  // BH_OPEN_INSIDE: one particle per lane, group 1
+    bool quad;         // BH_QUADRUPOLE: one particle per lane, group 1, Kahan
 };
 
 // kahan / potential / counting variants; returns number of kernel launches

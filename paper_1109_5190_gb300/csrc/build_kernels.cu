@@ -372,7 +372,8 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
              const SysDyn *__restrict__ dyn, const uint64_t *__restrict__ key,
              const uint32_t *__restrict__ noff, const float4 *__restrict__ spos,
              WNode *__restrict__ nodeW, int4 *__restrict__ nodeR, double4_32a *__restrict__ nodeD,
-             uint32_t *__restrict__ nlist, Small *__restrict__ sm)
+             uint32_t *__restrict__ nlist, double *__restrict__ nodeI, float4 *__restrict__ nodeQ,
+             Small *__restrict__ sm)
 {
     if (halted(sm)) return;
     __shared__ unsigned h[kNumLevels], base[kNumLevels];
@@ -433,12 +434,22 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
                 const float4 p = spos[j];
                 nodeW[n].a = p;
                 nodeD[n] = make_double4_32a(p.w, p.x, p.y, p.z);
+                if (nodeI) {  // no second moments about itself
+                    for (int q = 0; q < 6; ++q) nodeI[6 * (size_t)n + q] = 0.0;
+                    nodeQ[2 * (size_t)n] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    nodeQ[2 * (size_t)n + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             }
             if (l == 0) {
                 if (count == 1) {
                     const float4 p = spos[j];
                     nodeW[n].a = p;
                     nodeD[n] = make_double4_32a(p.w, p.x, p.y, p.z);
+                    if (nodeI) {
+                        for (int q = 0; q < 6; ++q) nodeI[6 * (size_t)n + q] = 0.0;
+                        nodeQ[2 * (size_t)n] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        nodeQ[2 * (size_t)n + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
                 } else {
                     const double cx = D.mx[0] / D.mtot, cy = D.mx[1] / D.mtot, cz = D.mx[2] / D.mtot;
                     const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
@@ -459,9 +470,45 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
 // children (first child = next node, then skip pointers):
 // M = sum m_c, com = sum m_c com_c / M.  The FP64 result is kept (nodeD) and
 // split into an FP32 high part and a packed low part for the walk.
+// Quadrupole mode: second moments I_ab = sum m r_a r_b about the node's centre
+// of mass (cx, cy, cz), in FP64: a bucket sums its particles; an internal node
+// sums its children's moments moved to its own centre (parallel axes:
+// I_child + m_child (c_child - c)(c_child - c)^T), in a second pass over the
+// children once the centre is known.  Also writes the FP32 copy for the walk.
+__device__ __noinline__ void second_moments(unsigned n, int4 C, float crit, int skip, double cx,
+                                            double cy, double cz,
+                                            const float4 *__restrict__ spos,
+                                            const WNode *__restrict__ nodeW,
+                                            const double4_32a *__restrict__ nodeD,
+                                            double *__restrict__ nodeI, float4 *__restrict__ nodeQ)
+{
+    double I[6] = {0, 0, 0, 0, 0, 0};
+    if (crit == kBucketCrit) {
+        for (int q = C.x; q < C.x + C.y; ++q) {
+            const float4 p = spos[q];
+            const double m = p.w, r0 = p.x - cx, r1 = p.y - cy, r2 = p.z - cz;
+            I[0] += m * r0 * r0; I[1] += m * r1 * r1; I[2] += m * r2 * r2;
+            I[3] += m * r0 * r1; I[4] += m * r0 * r2; I[5] += m * r1 * r2;
+        }
+    } else {
+        for (int ch = (int)n + 1; ch < skip; ch = wn_skip(nodeW[ch].b)) {
+            const double4_32a d = nodeD[ch];
+            const double *Ic = nodeI + 6 * (size_t)ch;
+            const double r0 = d.y - cx, r1 = d.z - cy, r2 = d.w - cz;
+            I[0] += Ic[0] + d.x * r0 * r0; I[1] += Ic[1] + d.x * r1 * r1;
+            I[2] += Ic[2] + d.x * r2 * r2; I[3] += Ic[3] + d.x * r0 * r1;
+            I[4] += Ic[4] + d.x * r0 * r2; I[5] += Ic[5] + d.x * r1 * r2;
+        }
+    }
+    for (int q = 0; q < 6; ++q) nodeI[6 * (size_t)n + q] = I[q];
+    nodeQ[2 * (size_t)n] = make_float4((float)I[0], (float)I[1], (float)I[2], (float)I[3]);
+    nodeQ[2 * (size_t)n + 1] = make_float4((float)I[4], (float)I[5], 0.f, 0.f);
+}
+
 __device__ __forceinline__ void com_node(unsigned n, const float4 *__restrict__ spos,
                                          WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR,
-                                         double4_32a *__restrict__ nodeD)
+                                         double4_32a *__restrict__ nodeD, double *__restrict__ nodeI,
+                                         float4 *__restrict__ nodeQ)
 {
     const int4 C = nodeR[n];  // first, count, level
     const uint4 B = nodeW[n].b;
@@ -492,19 +539,20 @@ __device__ __forceinline__ void com_node(unsigned n, const float4 *__restrict__ 
     nodeD[n] = make_double4_32a(M, cx, cy, cz);
     nodeW[n].a = make_float4(hx, hy, hz, (float)M);
     nodeW[n].b = wn_pack(crit, skip, cx, cy, cz, hx, hy, hz);
+    if (nodeI) second_moments(n, C, crit, skip, cx, cy, cz, spos, nodeW, nodeD, nodeI, nodeQ);
 }
 
 // One level, all blocks.
 __global__ void __launch_bounds__(256)
 k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
             WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4_32a *__restrict__ nodeD,
-            const Small *__restrict__ sm)
+            double *__restrict__ nodeI, float4 *__restrict__ nodeQ, const Small *__restrict__ sm)
 {
     if (halted(sm)) return;
     const unsigned cnt = sm->level_cnt[l];
     const unsigned off = sm->level_off[l];
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x)
-        com_node(nlist[off + k], spos, nodeW, nodeR, nodeD);
+        com_node(nlist[off + k], spos, nodeW, nodeR, nodeD, nodeI, nodeQ);
 }
 
 // The deep levels l_hi .. l_lo, which hold few nodes, in one block: a block
@@ -512,16 +560,35 @@ k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict_
 __global__ void __launch_bounds__(1024)
 k_com_deep(int l_hi, int l_lo, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
            WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4_32a *__restrict__ nodeD,
-           const Small *__restrict__ sm)
+           double *__restrict__ nodeI, float4 *__restrict__ nodeQ, const Small *__restrict__ sm)
 {
     if (halted(sm)) return;
     for (int l = l_hi; l >= l_lo; --l) {
         const unsigned cnt = sm->level_cnt[l];
         const unsigned off = sm->level_off[l];
         for (unsigned k = threadIdx.x; k < cnt; k += blockDim.x)
-            com_node(nlist[off + k], spos, nodeW, nodeR, nodeD);
+            com_node(nlist[off + k], spos, nodeW, nodeR, nodeD, nodeI, nodeQ);
         __syncthreads();
     }
+}
+
+// Quadrupole mode: each system's root (written by the topology pass, centre
+// of mass from the FP64 reduction) gets its second moments from its children
+// once level 1 is done.  One thread per system.
+__global__ void k_root_moments(const SysStatic *__restrict__ sys,
+                               const uint32_t *__restrict__ noff, const float4 *__restrict__ spos,
+                               const WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR,
+                               const double4_32a *__restrict__ nodeD, double *__restrict__ nodeI,
+                               float4 *__restrict__ nodeQ, const Small *__restrict__ sm)
+{
+    if (halted(sm) || threadIdx.x != 0) return;
+    const SysStatic S = sys[blockIdx.x];
+    const unsigned n = noff[S.start];
+    const int4 C = nodeR[n];
+    if (C.y < 2) return;  // a one-particle root is a leaf (moments zero)
+    const double4_32a D = nodeD[n];
+    const uint4 B = nodeW[n].b;
+    second_moments(n, C, wn_crit(B), wn_skip(B), D.y, D.z, D.w, spos, nodeW, nodeD, nodeI, nodeQ);
 }
 
 // ------------------------------------------------------ closing kick (A8)
@@ -740,7 +807,7 @@ void launch_topology(const BuildBufs &b, cudaStream_t st)
     k_level_offsets<<<1, 32, 0, st>>>(b.small, b.noff, b.n_total, b.node_cap);
     k_topo_write<<<b.nchunks, kWideThreads, 0, st>>>(b.chunks, b.sys, b.dyn, b.key0, b.noff,
                                                       b.spos, b.nodeW, b.nodeR, b.nodeD, b.nlist,
-                                                      b.small);
+                                                      b.nodeI, b.nodeQ, b.small);
     g_launches += 2;
 }
 
@@ -750,14 +817,23 @@ void launch_com(const BuildBufs &b, cudaStream_t st)
     int l = kLevels;
     if (b.deep_cut <= kLevels) {
         k_com_deep<<<1, 1024, 0, st>>>(kLevels, b.deep_cut, b.nlist, b.spos, b.nodeW, b.nodeR,
-                                       b.nodeD, b.small);
+                                       b.nodeD, b.nodeI, b.nodeQ, b.small);
         g_launches += 1;
         l = b.deep_cut - 1;
     }
     for (; l >= 1; --l) {
-        k_com_level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeW, b.nodeR, b.nodeD, b.small);
+        k_com_level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeW, b.nodeR, b.nodeD,
+                                          b.nodeI, b.nodeQ, b.small);
         g_launches += 1;
     }
+    if (b.nodeI) launch_root_moments(b, st);
+}
+
+void launch_root_moments(const BuildBufs &b, cudaStream_t st)
+{
+    k_root_moments<<<b.nsys, 32, 0, st>>>(b.sys, b.noff, b.spos, b.nodeW, b.nodeR, b.nodeD,
+                                           b.nodeI, b.nodeQ, b.small);
+    g_launches += 1;
 }
 
 void launch_kick(const BuildBufs &b, cudaStream_t st)

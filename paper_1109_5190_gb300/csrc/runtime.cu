@@ -183,7 +183,7 @@ struct Forest {
     bool tables_dirty = true;
 
     DevBuf d_sys, d_dyn, d_chunks, d_mode, d_parts, key0, key1, val0, val1, rs_counts, scan_part,
-        spos, ncount, noff, nodeW, nodeR, nodeD, nlist, d_small, d_diag_parts, d_diag_out,
+        spos, ncount, noff, nodeW, nodeR, nodeD, nlist, nodeI, nodeQ, d_small, d_diag_parts, d_diag_out,
         d_counts, d_export;
     unsigned node_cap = 0;
     struct TileSet {
@@ -290,6 +290,8 @@ struct Forest {
         b.nodeR = nodeR.as<int4>();
         b.nodeD = nodeD.as<double4_32a>();
         b.nlist = nlist.as<uint32_t>();
+        b.nodeI = quad() ? nodeI.as<double>() : nullptr;
+        b.nodeQ = quad() ? nodeQ.as<float4>() : nullptr;
         b.node_cap = node_cap;
         b.small = small();
         b.n_total = n_total;
@@ -305,6 +307,10 @@ struct Forest {
         TRY(nodeR.ensure(cap * sizeof(int4)));
         TRY(nodeD.ensure(cap * sizeof(double4_32a)));
         TRY(nlist.ensure(cap * sizeof(uint32_t)));
+        if (quad()) {
+            TRY(nodeI.ensure(cap * 6 * sizeof(double)));
+            TRY(nodeQ.ensure(cap * 2 * sizeof(float4)));
+        }
         node_cap = (unsigned)cap;
         invalidate_graph();
         return BH_OK;
@@ -441,6 +447,7 @@ struct Forest {
     {
         WalkArgs a;
         a.nodeW = nodeW.as<WNode>();
+        a.nodeQ = quad() ? nodeQ.as<float4>() : nullptr;
         a.nodeR = nodeR.as<int4>();
         a.nodeD = nodeD.as<double4_32a>();
         a.dyn = d_dyn.as<SysDyn>();
@@ -459,14 +466,17 @@ struct Forest {
         return a;
     }
 
-    // BH_OPEN_INSIDE fixes the shape to one particle per lane
+    // BH_OPEN_INSIDE and BH_QUADRUPOLE fix the shape to one particle per lane
     WalkShape shape() const
     {
-        if (open_inside())
-            return WalkShape{1, tune.warps_per_block, tune.blocks_per_sm, 1, true};
-        return WalkShape{tune.ppl, tune.warps_per_block, tune.blocks_per_sm, tune.group, false};
+        if (fixed_shape())
+            return WalkShape{1, tune.warps_per_block, tune.blocks_per_sm, 1, open_inside(), quad()};
+        return WalkShape{tune.ppl, tune.warps_per_block, tune.blocks_per_sm, tune.group, false,
+                         false};
     }
     bool open_inside() const { return (flags & BH_OPEN_INSIDE) != 0; }
+    bool quad() const { return (flags & BH_QUADRUPOLE) != 0; }
+    bool fixed_shape() const { return open_inside() || quad(); }
     bool kahan() const { return !(flags & BH_NO_KAHAN); }
     bool pot() const { return (flags & BH_POTENTIAL) != 0; }
 
@@ -723,8 +733,8 @@ struct Forest {
             for (int w : warps) {
                 for (int share : shares) {
                     bh_tuning t{p, w, 0, g, share};
-                    if (open_inside() && (g != 1 || p != 1)) continue;
-                    WalkShape sh{p, w, 0, g, open_inside()};
+                    if (fixed_shape() && (g != 1 || p != 1)) continue;
+                    WalkShape sh{p, w, 0, g, open_inside(), quad()};
                     if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0) continue;
                     tune = t;  // walk_args reads the static share from tune
                     float ms_best = 1e30f;
@@ -772,9 +782,10 @@ struct Forest {
                                         "ppl 1/2, group 2, 0 or BH_GROUP_LIST with ppl 1; warps "
                                         "1..16; static_share 0..90; blocks_per_sm >= 0)");
         // the shape as it would be launched (BH_OPEN_INSIDE: one particle per lane)
-        const WalkShape sh = open_inside()
-                                 ? WalkShape{1, t->warps_per_block, t->blocks_per_sm, 1, true}
-                                 : WalkShape{t->ppl, t->warps_per_block, t->blocks_per_sm, t->group, false};
+        const WalkShape sh =
+            fixed_shape()
+                ? WalkShape{1, t->warps_per_block, t->blocks_per_sm, 1, open_inside(), quad()}
+                : WalkShape{t->ppl, t->warps_per_block, t->blocks_per_sm, t->group, false, false};
         if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0)
             return fail(BH_ERR_INVALID, "walk shape does not fit on an SM");
         tune = *t;
@@ -800,7 +811,7 @@ struct Forest {
         TRY(ensure_tiles(1));
         TRY(clear_status());
         reset_step_counters();
-        WalkShape sh{1, 8, 0, open_inside() ? 1 : tune.group, open_inside()};
+        WalkShape sh{1, 8, 0, fixed_shape() ? 1 : tune.group, open_inside(), quad()};
         CKR(cudaMemsetAsync(small()->wstats, 0, sizeof(small()->wstats), st));
         launch_walk(walk_args(1, d_counts.as<uint32_t>()), sh, true, false, true, nsm, st);
         launches += 1;
@@ -929,8 +940,10 @@ static int check_bh_params(const bh_params *p)
     TRY(check_params(p->G, p->eps, p->theta));
     if (p->max_depth != BH_MAX_DEPTH) return fail(BH_ERR_INVALID, "max_depth must be 21");
     if (p->leaf_cap != 1) return fail(BH_ERR_INVALID, "leaf_cap must be 1");
-    if (p->flags & ~(BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE))
+    if (p->flags & ~(BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE | BH_QUADRUPOLE))
         return fail(BH_ERR_INVALID, "unknown params flags");
+    if ((p->flags & BH_QUADRUPOLE) && (p->flags & BH_NO_KAHAN))
+        return fail(BH_ERR_INVALID, "BH_QUADRUPOLE needs Kahan sums");
     return BH_OK;
 }
 
@@ -1136,8 +1149,10 @@ int bh_forest_create(bh_forest **out, int nsys, const bh_system_desc *d, void *s
     if (!out) return fail(BH_ERR_INVALID, "null out");
     *out = nullptr;
     if (nsys < 1 || !d) return fail(BH_ERR_INVALID, "need at least one system");
-    if (flags & ~(BH_DEVICE_PTRS | BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE))
+    if (flags & ~(BH_DEVICE_PTRS | BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE | BH_QUADRUPOLE))
         return fail(BH_ERR_INVALID, "unknown flags");
+    if ((flags & BH_QUADRUPOLE) && (flags & BH_NO_KAHAN))
+        return fail(BH_ERR_INVALID, "BH_QUADRUPOLE needs Kahan sums");
     for (int s = 0; s < nsys; ++s) {
         if (d[s].n < 1 || !d[s].pos_mass) return fail(BH_ERR_INVALID, "system " + std::to_string(s) + ": n < 1 or null pos_mass");
         TRY(check_params(d[s].G, d[s].eps, d[s].theta));
@@ -1145,7 +1160,7 @@ int bh_forest_create(bh_forest **out, int nsys, const bh_system_desc *d, void *s
     std::unique_ptr<bh_forest> F(new (std::nothrow) bh_forest);
     if (!F) return fail(BH_ERR_OOM, "host allocation failed");
     Forest &f = F->f;
-    TRY(f.init(stream, flags & (BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE)));
+    TRY(f.init(stream, flags & (BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE | BH_QUADRUPOLE)));
     f.tune.static_share = nsys > 1 ? 0 : f.tune.static_share;  // uneven tiles: all dynamic
     TRY(f.begin_call());
     for (int s = 0; s < nsys; ++s) {
@@ -1285,10 +1300,11 @@ struct Job {
 // its share of the forest's scratch (two key and two id buffers, the sorted
 // copy, node counts and offsets) and of the node arrays (WNode 32 B, nodeR
 // 16 B, nodeD 32 B, level-list entry 4 B; up to ~2 nodes per particle with
-// the growth margin).
-size_t job_bytes(int64_t n)
+// the growth margin; in quadrupole mode also the second moments).
+size_t job_bytes(int64_t n, bool quad)
 {
-    const size_t per = 5 * 16 + (8 + 8 + 4 + 4 + 16 + 4 + 4) + 2 * (32 + 16 + 32 + 4);
+    const size_t per = 5 * 16 + (8 + 8 + 4 + 4 + 16 + 4 + 4) + 2 * (32 + 16 + 32 + 4) +
+                       (quad ? 2 * (6 * 8 + 2 * 16) : 0);  // second moments, FP64 + FP32
     return (size_t)n * per + 4096 * 64;
 }
 
@@ -1459,8 +1475,10 @@ int bh_server_create(bh_server **out, size_t hbm_budget, int max_slots, void *st
     if (!out) return fail(BH_ERR_INVALID, "null out");
     *out = nullptr;
     if (max_slots < 1 || hbm_budget < (1u << 20)) return fail(BH_ERR_INVALID, "bad budget or slot count");
-    if (flags & ~(BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE))
+    if (flags & ~(BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE | BH_QUADRUPOLE))
         return fail(BH_ERR_INVALID, "unknown flags");
+    if ((flags & BH_QUADRUPOLE) && (flags & BH_NO_KAHAN))
+        return fail(BH_ERR_INVALID, "BH_QUADRUPOLE needs Kahan sums");
     std::unique_ptr<bh_server> s(new (std::nothrow) bh_server);
     if (!s) return fail(BH_ERR_OOM, "host allocation failed");
     s->budget = hbm_budget;
@@ -1492,7 +1510,7 @@ int bh_submit(bh_server *s, const bh_request *r, uint64_t *ticket)
     j->n = r->n;
     j->G = r->G; j->eps = r->eps; j->theta = r->theta; j->dt = r->dt;
     j->nsteps = r->nsteps;
-    j->bytes = job_bytes(r->n);
+    j->bytes = job_bytes(r->n, (s->flags & BH_QUADRUPOLE) != 0);
     if (j->bytes > s->budget) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stats.rejected++;

@@ -169,6 +169,44 @@ __device__ __forceinline__ void bucket_sum(const int4 *__restrict__ nodeR,
     }
 }
 
+// Quadrupole mode: an accepted cell's monopole plus its second-order term.
+// With d = com - x, s^2 = |d|^2 + eps^2 and I the cell's second moments about
+// its centre of mass (FP32 copy: (xx, yy, zz, xy), (xz, yz, -, -)), the
+// softened kernel expanded to second order gives, before the factor G,
+//   a   += m d / s^3 - 3 (I d) / s^5 + ((15/2) (d.I.d) / s^7 - (3/2) tr I / s^5) d
+//   phi -= m / s + (1/2) (3 (d.I.d) / s^5 - tr I / s^3)
+// (the potential sum pp holds minus phi / G).
+template <bool KAHAN, bool POT, bool COUNT>
+__device__ __forceinline__ void interact_quad(const float4 *Qp, float m, float dx, float dy,
+                                              float dz, float d2, float eps2, float &ax, float &ay,
+                                              float &az, float &cx, float &cy, float &cz,
+                                              float &pp, float &cp, unsigned &cnt)
+{
+    float q[8];
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(q[0]), "=f"(q[1]), "=f"(q[2]), "=f"(q[3]), "=f"(q[4]), "=f"(q[5]), "=f"(q[6]),
+          "=f"(q[7])
+        : "l"(Qp));
+    const float r2 = d2 + eps2;
+    const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float inv2 = inv * inv;
+    const float inv3 = inv2 * inv;
+    const float inv5 = inv3 * inv2;
+    const float inv7 = inv5 * inv2;
+    const float Id0 = fmaf(q[0], dx, fmaf(q[3], dy, q[4] * dz));
+    const float Id1 = fmaf(q[3], dx, fmaf(q[1], dy, q[5] * dz));
+    const float Id2 = fmaf(q[4], dx, fmaf(q[5], dy, q[2] * dz));
+    const float dId = fmaf(dx, Id0, fmaf(dy, Id1, dz * Id2));
+    const float tr = q[0] + q[1] + q[2];
+    const float c = fmaf(7.5f * dId, inv7, fmaf(m, inv3, -1.5f * tr * inv5));
+    const float t5 = -3.f * inv5;
+    acc_add<KAHAN>(ax, cx, fmaf(c, dx, t5 * Id0));
+    acc_add<KAHAN>(ay, cy, fmaf(c, dy, t5 * Id1));
+    acc_add<KAHAN>(az, cz, fmaf(c, dz, t5 * Id2));
+    if (POT) acc_add<KAHAN>(pp, cp, fmaf(m, inv, 0.5f * fmaf(3.f * dId, inv5, -tr * inv3)));
+    if (COUNT) cnt += 1;
+}
+
 // GROUP = 32: the warp votes (__reduce_min_sync) on the next node and visits
 // the union of its particles' traversals, one broadcast node load per step.
 // GROUP = 4, 8, 16: aligned lane groups vote among themselves (xor-shuffle
@@ -180,7 +218,8 @@ __device__ __forceinline__ void bucket_sum(const int4 *__restrict__ nodeR,
 // order, so its sums -- and the results -- do not depend on the shape.
 // Register budget: a block of up to 512 threads, and enough blocks per SM
 // for 48 resident warps with one particle per lane.
-template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false>
+template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false,
+          bool QUAD = false>
 __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
 {
     static_assert(GROUP == 1 || GROUP == 2 || GROUP == 4 || GROUP == 8 || GROUP == 16 ||
@@ -301,9 +340,15 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
                     if (acc) {
                         // the potential leaves out the particle's own leaf
                         const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[cur].x) == myj[k];
-                        interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self,
-                                                    ax[k], ay[k], az[k], cx[k], cy[k], cz[k],
-                                                    pp[k], cp[k], cnt[k]);
+                        if (QUAD && crit >= 0.f)  // a cell, not a leaf
+                            interact_quad<KAHAN, POT, COUNT>(a.nodeQ + 2 * (size_t)cur, A.w, dx, dy,
+                                                             dz, d2, eps2, ax[k], ay[k], az[k],
+                                                             cx[k], cy[k], cz[k], pp[k], cp[k],
+                                                             cnt[k]);
+                        else
+                            interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self,
+                                                        ax[k], ay[k], az[k], cx[k], cy[k], cz[k],
+                                                        pp[k], cp[k], cnt[k]);
                         nxt[k] = skip;
                     } else if (crit == kBucketCrit) {
                         bucket_sum<KAHAN, POT, COUNT>(a.nodeR, a.spos, cur, px[k], py[k], pz[k],
@@ -715,18 +760,19 @@ __global__ void __launch_bounds__(512, 3) k_walk_list(WalkArgs a)
 
 // Blocks of `warps` warps that fit on one SM, queried once per variant and
 // block size (never during stream capture: callers query before capturing).
-template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false>
+template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false,
+          bool QUAD = false>
 int occupancy(int warps)
 {
     static int cache[33] = {0};
     if (warps < 1 || warps > 32) return 0;
     if (cache[warps] == 0) {
         // the walk uses no shared memory: give the SM's unified storage to L1
-        cudaFuncSetAttribute(k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN>,
+        cudaFuncSetAttribute(k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, 0);
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &occ, k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN>, warps * 32, 0) != cudaSuccess)
+                &occ, k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD>, warps * 32, 0) != cudaSuccess)
             occ = 0;
         cache[warps] = occ > 0 ? occ : -1;
     }
@@ -811,41 +857,49 @@ int launch_list(const WalkArgs *a, const WalkShape &sh, int nsm, cudaStream_t st
     return occ;
 }
 
-template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false>
+template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false,
+          bool QUAD = false>
 void launch_one(const WalkArgs &a, const WalkShape &sh, int nsm, cudaStream_t st)
 {
     const int threads = sh.warps * 32;
     int bps = sh.blocks_per_sm;
-    if (bps <= 0) bps = occupancy<PPL, GROUP, KAHAN, POT, COUNT, OPEN>(sh.warps);
+    if (bps <= 0) bps = occupancy<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD>(sh.warps);
     if (bps <= 0) bps = 1;
-    k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN><<<nsm * bps, threads, 0, st>>>(a);
+    k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD><<<nsm * bps, threads, 0, st>>>(a);
 }
 
-// The walk under the alternative opening rule (BH_OPEN_INSIDE): one particle
-// per lane, no vote.
+template <bool KAHAN, bool POT, bool COUNT, bool OPEN, bool QUAD>
+int fixed_one(const WalkArgs *a, const WalkShape &sh, int nsm, cudaStream_t st)
+{
+    if (a) launch_one<1, 1, KAHAN, POT, COUNT, OPEN, QUAD>(*a, sh, nsm, st);
+    return occupancy<1, 1, KAHAN, POT, COUNT, OPEN, QUAD>(sh.warps);
+}
+
+// The walks with a fixed shape (one particle per lane, no vote): the
+// alternative opening rule (BH_OPEN_INSIDE) and the quadrupole term
+// (BH_QUADRUPOLE, Kahan sums only).  Counting needs no quadrupole term: the
+// accepted sets are the same.
 template <bool COUNT>
-int run_open(bool kahan, bool pot, const WalkArgs *a, const WalkShape &sh, int nsm,
-             cudaStream_t st)
+int run_fixed(bool kahan, bool pot, const WalkArgs *a, const WalkShape &sh, int nsm,
+              cudaStream_t st)
 {
     if (sh.ppl != 1 || sh.group != 1) return 0;
-    if (COUNT) {
-        if (a) launch_one<1, 1, true, false, true, true>(*a, sh, nsm, st);
-        return occupancy<1, 1, true, false, true, true>(sh.warps);
+    const bool open = sh.open_inside;
+    if (COUNT)
+        return open ? fixed_one<true, false, true, true, false>(a, sh, nsm, st)
+                    : fixed_one<true, false, true, false, false>(a, sh, nsm, st);
+    if (sh.quad) {
+        if (!kahan) return 0;
+        if (open)
+            return pot ? fixed_one<true, true, false, true, true>(a, sh, nsm, st)
+                       : fixed_one<true, false, false, true, true>(a, sh, nsm, st);
+        return pot ? fixed_one<true, true, false, false, true>(a, sh, nsm, st)
+                   : fixed_one<true, false, false, false, true>(a, sh, nsm, st);
     }
-    if (kahan && pot) {
-        if (a) launch_one<1, 1, true, true, false, true>(*a, sh, nsm, st);
-        return occupancy<1, 1, true, true, false, true>(sh.warps);
-    }
-    if (kahan) {
-        if (a) launch_one<1, 1, true, false, false, true>(*a, sh, nsm, st);
-        return occupancy<1, 1, true, false, false, true>(sh.warps);
-    }
-    if (pot) {
-        if (a) launch_one<1, 1, false, true, false, true>(*a, sh, nsm, st);
-        return occupancy<1, 1, false, true, false, true>(sh.warps);
-    }
-    if (a) launch_one<1, 1, false, false, false, true>(*a, sh, nsm, st);
-    return occupancy<1, 1, false, false, false, true>(sh.warps);
+    if (kahan && pot) return fixed_one<true, true, false, true, false>(a, sh, nsm, st);
+    if (kahan) return fixed_one<true, false, false, true, false>(a, sh, nsm, st);
+    if (pot) return fixed_one<false, true, false, true, false>(a, sh, nsm, st);
+    return fixed_one<false, false, false, true, false>(a, sh, nsm, st);
 }
 
 // Dispatch of the runtime shape onto the compiled variants.
@@ -879,7 +933,7 @@ struct Variants {
     static int run(bool kahan, bool pot, const WalkArgs *a, const WalkShape &sh, int nsm,
                    cudaStream_t st)
     {
-        if (sh.open_inside) return run_open<COUNT>(kahan, pot, a, sh, nsm, st);
+        if (sh.open_inside || sh.quad) return run_fixed<COUNT>(kahan, pot, a, sh, nsm, st);
         if (sh.group == BH_GROUP_LIST) {  // interaction lists
             if (COUNT) return launch_list<true, false, true>(a, sh, nsm, st);
             if (kahan && pot) return launch_list<true, true, false>(a, sh, nsm, st);
@@ -939,7 +993,7 @@ int walk_max_blocks_per_sm(const WalkShape &sh, bool kahan, bool pot)
 {
     WalkShape cs = sh;
     cs.ppl = 1;
-    if (cs.open_inside) cs.group = 1;
+    if (cs.open_inside || cs.quad) cs.group = 1;
     Variants<true>::run(true, false, nullptr, cs, 0, nullptr);  // the counting variant too
     return Variants<false>::run(kahan, pot, nullptr, sh, 0, nullptr);
 }

@@ -461,6 +461,64 @@ def test_open_inside_rule_changes_nothing_below_its_threshold():
         B.bh_forest_destroy(f)
 
 
+@pytest.mark.parametrize("kind,n,seed", [("plummer", 5000, 51), ("uniform", 6000, 52),
+                                         ("dups", 1000, 53)])
+@pytest.mark.parametrize("theta", [0.5, 0.8])
+@pytest.mark.parametrize("open_inside", [False, True])
+def test_quadrupole_against_oracle(kind, n, seed, theta, open_inside):
+    # BH_QUADRUPOLE: every accepted cell adds its second-order term; forces and
+    # potentials against the oracle under the same rules, interaction counts
+    # the same as without the term, and a KDK step under it
+    pm, vel = gen(kind, n, seed)
+    fl = B.BH_POTENTIAL | B.BH_QUADRUPOLE | (B.BH_OPEN_INSIDE if open_inside else 0)
+    h = make(pm, vel, 0.01, theta, flags=fl)
+    try:
+        a = gpu_accel(h, n)
+        T = oracle.Tree(pm)
+        ref, pot, cnt = T.accel(theta, 0.01, open_inside=open_inside, quadrupole=True)
+        assert_accel_close(a, ref, what=f"quadrupole {kind} theta={theta}")
+        e = np.abs(a[:, 3] - pot) / np.abs(pot)
+        assert np.percentile(e, 99) <= 1e-5 and e.max() <= 1e-3
+        gc, _ = B.bh_interaction_count(h, n)
+        assert np.array_equal(gc.astype(np.int64), cnt)
+        B.bh_step(h, 2, 1e-3)
+        x = np.zeros_like(pm); a = np.zeros_like(pm)
+        B.bh_get_state(h, x, None, a)
+        ref, _, _ = oracle.Tree(x).accel(theta, 0.01, open_inside=open_inside, quadrupole=True)
+        assert_accel_close(a, ref, what=f"quadrupole {kind} theta={theta} step 2")
+    finally:
+        B.bh_destroy(h)
+
+
+def test_quadrupole_forest_and_error_against_direct_sum():
+    # in a forest every system gets its own second moments (roots included);
+    # and the term brings the forces closer to the direct sum
+    systems = synth.forest_systems(5, 256, 5000, seed=54, theta=0.7, eps=0.01)
+    descs = [dict(pos_mass=s.pos_mass, vel=s.vel, eps=0.01, theta=0.7, dt=1e-3) for s in systems]
+    f = B.bh_forest_create(descs, flags=B.BH_QUADRUPOLE)
+    try:
+        B.bh_forest_compute_accel(f)
+        for k, d in enumerate(descs):
+            n = len(d["pos_mass"])
+            af = np.zeros((n, 4), np.float32)
+            B.bh_forest_get_state(f, k, None, None, af)
+            ref, _, _ = oracle.Tree(d["pos_mass"]).accel(0.7, 0.01, quadrupole=True)
+            assert_accel_close(af, ref, what=f"quadrupole forest system {k}")
+    finally:
+        B.bh_forest_destroy(f)
+    pm, vel = synth.plummer(4000, 55)
+    ad, _ = oracle.direct(pm, 0.01)
+    errs = []
+    for fl in (0, B.BH_QUADRUPOLE):
+        h = make(pm, vel, 0.01, 0.7, flags=fl)
+        try:
+            a = gpu_accel(h, 4000)
+        finally:
+            B.bh_destroy(h)
+        errs.append(np.median(np.linalg.norm(a[:, :3] - ad, axis=1) / np.linalg.norm(ad, axis=1)))
+    assert errs[1] < 0.6 * errs[0], errs
+
+
 def test_uniform_cube_million_step0_all_particles():
     # uniform cube N = 2^20, eps = 0.005, theta in {0.5, 0.7}, 20 KDK steps of
     # dt = 5e-4: every particle against the oracle at step 0, then a seeded

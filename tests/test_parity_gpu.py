@@ -519,6 +519,26 @@ def test_quadrupole_forest_and_error_against_direct_sum():
     assert errs[1] < 0.6 * errs[0], errs
 
 
+@pytest.mark.parametrize("offset", [(1.0e3, -2.0e3, 5.0e2), (3.0e5, 0.0, -1.0e5)])
+def test_system_far_from_the_origin(offset):
+    # a Plummer sphere moved far from the origin: FP32 coordinates keep fewer
+    # bits of the cloud's shape, the keys, the centre-of-mass low parts and the
+    # tie band must still reproduce the oracle (same FP32 inputs)
+    pm, vel = synth.plummer(6000, 61)
+    pm = pm.copy()
+    pm[:, :3] += np.asarray(offset, np.float32)
+    h = make(pm, vel, 0.01, 0.6)
+    try:
+        a = gpu_accel(h, 6000)
+        T = check_tree(h, pm)
+        ref, _, cnt = T.accel(0.6, 0.01)
+        assert_accel_close(a, ref, what=f"offset {offset}")
+        gc, _ = B.bh_interaction_count(h, 6000)
+        assert np.array_equal(gc.astype(np.int64), cnt)
+    finally:
+        B.bh_destroy(h)
+
+
 def test_uniform_cube_million_step0_all_particles():
     # uniform cube N = 2^20, eps = 0.005, theta in {0.5, 0.7}, 20 KDK steps of
     # dt = 5e-4: every particle against the oracle at step 0, then a seeded

@@ -322,6 +322,8 @@ def run_gpu(args):
 
     B.bh_destroy(h)
     extra = {}
+    if rank == 0 and not args.no_theta07 and args.workload == "uniform1m":
+        extra["theta_0.7"] = bench_other_theta(args, B, torch, 0.7)
     if rank == 0 and not args.no_batched:
         extra["batched"] = bench_batched(args, B, torch)
     if rank == 0 and not args.no_served:
@@ -422,6 +424,39 @@ def bench_batched(args, B, torch):
                                  "steps_per_system": args.plain_steps,
                                  "how": "bh_step on each system in turn, kernels launched directly"},
             "speedup_vs_plain": batched / plain}
+
+
+def bench_other_theta(args, B, torch, theta):
+    """The headline workload (uniform cube of 2^20 particles, eps 0.005, dt
+    5e-4) at another opening angle: the same KDK steps from a captured graph,
+    autotuned, device time from the library's phase events."""
+    pm, vel = make_inputs()
+    d_pm = torch.from_numpy(pm).cuda()
+    d_vel = torch.from_numpy(vel).cuda()
+    h = B.bh_create(B.params(1.0, EPS, theta), d_pm, d_vel, torch.cuda.current_stream())
+    del d_pm, d_vel
+    try:
+        shape = B.bh_autotune(h)
+        B.bh_compute_accel(h)
+        B.bh_profile_begin(h)
+        B.bh_step(h, 1, DT, True)  # capture + warm-up
+        B.bh_profile_end(h)
+        torch.cuda.synchronize()
+        B.bh_profile_begin(h)
+        for _ in range(args.steps):
+            B.bh_step(h, 1, DT, True)
+        phase_ms, nst, _ = B.bh_profile_end(h)
+        stats = B.bh_walk_stats(h)
+    finally:
+        B.bh_destroy(h)
+    step_ms = float(phase_ms.sum()) / nst
+    return {"workload": WORKLOAD.replace(f"theta={THETA}", f"theta={theta}"),
+            "value": N_PART / (step_ms * 1e-3),
+            "unit": UNIT, "ms_per_step": step_ms,
+            "phase_ms_per_step": {k: float(v) / nst for k, v in
+                                  zip(("integrate", "build", "walk"), phase_ms)},
+            "walk_shape": list(shape),
+            "interactions_per_particle": stats["interactions"] / N_PART}
 
 
 def bench_large(args, B, torch, fma_peak_tflops, hbm_gbs):
@@ -557,6 +592,8 @@ def main():
     ap.add_argument("--static-share", type=int, default=75)
     ap.add_argument("--no-graph", action="store_true", help="launch each step's kernels directly")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-theta07", action="store_true",
+                    help="skip the headline workload at theta 0.7")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--forest-systems", type=int, default=512)

@@ -146,10 +146,13 @@ class Tree:
         return o, k
 
     def accel(self, theta: float, eps: float, G: float = 1.0, targets=None,
-              nthreads: int = 0, open_inside: bool = False, quadrupole: bool = False):
+              nthreads: int = 0, open_inside: bool = False, quadrupole: bool = False,
+              bmax: bool = False):
         """(acc (nt,3), pot (nt,), count (nt,)) for the target input indices.
         open_inside: never accept a cell that contains the particle;
-        quadrupole: accepted cells add their second-order term."""
+        quadrupole: accepted cells add their second-order term;
+        bmax: the opening test uses b_max (centre of mass to the cell's
+        farthest corner) for the cell's size instead of its side."""
         if targets is None:
             nt, tp = self.n, None
         else:
@@ -160,7 +163,8 @@ class Tree:
         cnt = np.zeros(nt, np.int64)
         _load().oracle_accel(self._h, G, eps, theta, nt, _ptr(tp), _ptr(acc), _ptr(pot),
                              _ptr(cnt), int(nthreads),
-                             int(bool(open_inside)) | (2 if quadrupole else 0))
+                             int(bool(open_inside)) | (2 if quadrupole else 0)
+                             | (4 if bmax else 0))
         return acc, pot, cnt
 
 

@@ -28,6 +28,11 @@
  *     body iff s^2 < theta^2 d^2 (strict); theta = 0 never accepts, which is
  *     direct summation; leaves are always taken particle by particle
  *     (optionally, a cell that contains the particle is always opened);
+ *   - optional alternative size in that test (Section V names alternative
+ *     ways of computing the criterion as future work): b_max, the distance
+ *     from the centre of mass to the farthest corner of the cell, which bounds
+ *     the distance of every point of the cell from the centre of mass
+ *     (Salmon and Warren 1994); accept iff b_max^2 < theta^2 d^2;
  *   - keys: the bounding cube is anchored at the per-axis minimum of the FP32
  *     positions with side = the largest FP32 extent (1 if that is below 1e-30);
  *     each coordinate is quantised to 21 bits as
@@ -405,6 +410,7 @@ typedef struct {
     int64_t self;
     int open_inside;  /* never accept a cell that contains the particle */
     int quad;         /* add each accepted cell's quadrupole term */
+    int bmax;         /* the cell's size in the test is b_max, not s */
     double xi[3];
     nsum a[3], phi;
     int64_t count;
@@ -452,6 +458,31 @@ static void quad_term(walker *w, const onode *d)
     nsum_add(&w->phi, -0.5 * (3.0 * dId / s5 - tr / s3));
 }
 
+/* b_max^2 of a cell: the squared distance from its centre of mass to the
+ * farthest corner of its cube.  Per axis the cube is [c, c + s] with
+ * c = lo + q s, q the cell's integer position at its level (the key prefix
+ * de-interleaved: bit 2 of each octal digit is x, bit 1 y, bit 0 z), and the
+ * farther face is max(com - c, (c + s) - com). */
+static double cell_bmax2(const otree *t, const onode *d)
+{
+    double s = ldexp((double)t->side, -d->level);
+    uint64_t q[3] = {0, 0, 0};
+    for (int b = 0; b < d->level; ++b) {
+        unsigned digit = (unsigned)((d->prefix >> (3 * b)) & 7u);
+        q[0] |= (uint64_t)((digit >> 2) & 1u) << b;
+        q[1] |= (uint64_t)((digit >> 1) & 1u) << b;
+        q[2] |= (uint64_t)(digit & 1u) << b;
+    }
+    double e2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double c = (double)t->lo[a] + (double)q[a] * s;
+        double lo_gap = d->com[a] - c, hi_gap = (c + s) - d->com[a];
+        double e = lo_gap > hi_gap ? lo_gap : hi_gap;
+        e2 += e * e;
+    }
+    return e2;
+}
+
 static void walk(walker *w, int32_t ni)
 {
     const otree *t = w->t;
@@ -467,9 +498,10 @@ static void walk(walker *w, int32_t ni)
     double dx = d->com[0] - w->xi[0], dy = d->com[1] - w->xi[1], dz = d->com[2] - w->xi[2];
     double d2 = dx * dx + dy * dy + dz * dz;
     double s = ldexp((double)t->side, -d->level);
+    double r2 = w->bmax ? cell_bmax2(t, d) : s * s;
     /* the cell holds the particle iff its key starts with the cell's prefix */
     int inside = (t->keys[w->self] >> (3 * (21 - d->level))) == d->prefix;
-    if (s * s < w->theta2 * d2 && !(w->open_inside && inside)) {
+    if (r2 < w->theta2 * d2 && !(w->open_inside && inside)) {
         term(w, d->m, d->com, 0);
         if (w->quad) quad_term(w, d);
         return;
@@ -483,7 +515,9 @@ static void walk(walker *w, int32_t ni)
  * options bit 0: the alternative opening rule that never accepts a cell
  * containing the particle itself (the pure test can, for theta > 1/sqrt(3):
  * the particle's own mass then enters an approximated cell); bit 1: each
- * accepted cell adds its quadrupole (second-moment) term to the monopole. */
+ * accepted cell adds its quadrupole (second-moment) term to the monopole;
+ * bit 2: the cell's size in the opening test is b_max (cell_bmax2) instead of
+ * its side, i.e. accept iff b_max^2 < theta^2 d^2. */
 int oracle_accel(otree *t, double G, double eps, double theta, int64_t nt,
                  const int64_t *targets, double *acc, double *pot, int64_t *count,
                  int nthreads, int options)
@@ -504,6 +538,7 @@ int oracle_accel(otree *t, double G, double eps, double theta, int64_t nt,
         w.self = i;
         w.open_inside = (options & 1) != 0;
         w.quad = (options & 2) != 0;
+        w.bmax = (options & 4) != 0;
         for (int a = 0; a < 3; ++a) w.xi[a] = t->x[4 * i + a];
         walk(&w, t->dfs[0]);
         for (int a = 0; a < 3; ++a) acc[3 * k + a] = G * nsum_get(&w.a[a]);

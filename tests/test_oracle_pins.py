@@ -6,6 +6,7 @@ special case.  Paper references: Section I (one particle per leaf, centre of
 mass per cube), Section III and Fig. 1 (opening criterion), Fig. 2 (worked
 example).  No GPU needed.
 """
+import itertools
 import json
 import math
 import os
@@ -244,17 +245,30 @@ def test_error_decreases_as_theta_decreases(oracle_lib):
     assert errs[-1] < 1e-4
 
 
-def _frontier_accel(pm, theta, eps, lo_side, open_inside=False):
+def _quantised(x, lo, side):
+    """Level-21 integer position of each point by the key rule, in numpy FP32
+    arithmetic (independent of the oracle's key code)."""
+    scale = np.float32(2097152.0) / np.float32(side)
+    q = np.floor((x.astype(np.float32) - np.asarray(lo, np.float32)) * scale).astype(np.int64)
+    return np.clip(q, 0, 2 ** 21 - 1)
+
+
+def _frontier_accel(pm, theta, eps, lo_side, open_inside=False, bmax=False):
     """The Barnes-Hut sum from its set definition, without recursion: particle
     i uses every node whose proper ancestors all fail the opening test s^2 <
     theta^2 d^2 for i while the node itself passes it, is a one-particle leaf,
     or is a depth-cap bucket (then each member particle).  Nodes by brute-force
-    enumeration; centres of mass as direct sums over member particles."""
+    enumeration; centres of mass as direct sums over member particles.
+    bmax: the test's s is the largest distance from the centre of mass to one
+    of the cell's 8 corners (all enumerated), the cell placed by the integer
+    position of its first member at the cell's level."""
     nodes, order = _brute_force_nodes(pm)
     keys_sorted = oracle.keys(pm)[order]
     x = pm[order, :3]
     m = pm[order, 3]
     side = float(lo_side[1])
+    lo = np.asarray(lo_side[0], np.float32).astype(np.float64)
+    q21 = _quantised(x, lo_side[0], lo_side[1])
     com = {}
     for (lvl, pre, first, cnt, _) in nodes:
         mm = m[first:first + cnt]
@@ -265,6 +279,7 @@ def _frontier_accel(pm, theta, eps, lo_side, open_inside=False):
         xi = x[i]
 
         key_i = int(keys_sorted[i])
+        firsts = {(lvl, pre): first for (lvl, pre, first, cnt, _) in nodes}
 
         def opens(lvl, pre, cnt):
             if cnt == 1 or lvl == 21:
@@ -273,7 +288,13 @@ def _frontier_accel(pm, theta, eps, lo_side, open_inside=False):
                 return True
             M, c = com[(lvl, pre)]
             s = side * 2.0 ** -lvl
-            return not (s * s < theta * theta * float(((c - xi) ** 2).sum()))
+            if bmax:
+                c0 = lo + (q21[firsts[(lvl, pre)]] >> (21 - lvl)) * s
+                r2 = max(float(((c0 + np.array(b) * s - c) ** 2).sum())
+                         for b in itertools.product((0.0, 1.0), repeat=3))
+            else:
+                r2 = s * s
+            return not (r2 < theta * theta * float(((c - xi) ** 2).sum()))
 
         info = {(lvl, pre): cnt for (lvl, pre, first, cnt, _) in nodes}
         for (lvl, pre, first, cnt, _) in nodes:
@@ -298,11 +319,11 @@ def _frontier_accel(pm, theta, eps, lo_side, open_inside=False):
     return out_a, out_p, out_c
 
 
-@pytest.mark.parametrize("open_inside", [False, True])
+@pytest.mark.parametrize("rule", ["pure", "open_inside", "bmax", "bmax+open_inside"])
 @pytest.mark.parametrize("kind,n,seed", [("gauss", 40, 11), ("clustered", 60, 12),
                                          ("planar", 50, 13), ("dups", 30, 14)])
 @pytest.mark.parametrize("theta", [0.3, 0.5, 0.7, 1.0])
-def test_walk_equals_set_definition(oracle_lib, kind, n, seed, theta, open_inside):
+def test_walk_equals_set_definition(oracle_lib, kind, n, seed, theta, rule):
     # theta > 0: the recursive walk against the set definition of the sum it
     # computes, on inputs small enough to enumerate every node and ancestor
     if kind == "dups":
@@ -314,10 +335,11 @@ def test_walk_equals_set_definition(oracle_lib, kind, n, seed, theta, open_insid
         pm = pm.astype(np.float64)
     pm[:, 3] *= np.linspace(0.5, 1.5, n)  # unequal masses: a centroid is not the COM
     eps = 0.01
+    open_inside, bmax = "open_inside" in rule, "bmax" in rule
     T = oracle.Tree(pm)
-    a, p, c = T.accel(theta, eps, open_inside=open_inside)
+    a, p, c = T.accel(theta, eps, open_inside=open_inside, bmax=bmax)
     lo, side = T.cube()
-    wa, wp, wc = _frontier_accel(pm, theta, eps, (lo, side), open_inside)
+    wa, wp, wc = _frontier_accel(pm, theta, eps, (lo, side), open_inside, bmax)
     assert np.array_equal(c, wc)
     scale = np.abs(wa).max()
     assert np.abs(a - wa).max() <= 1e-12 * scale
@@ -475,3 +497,40 @@ def test_quadrupole_keeps_the_accepted_set(oracle_lib):
         _, _, c0 = T.accel(theta, 0.01)
         _, _, c1 = T.accel(theta, 0.01, quadrupole=True)
         assert np.array_equal(c0, c1)
+
+
+# ------------------------------------------------------ b_max opening rule
+
+def test_bmax_rule_between_two_pure_tests(oracle_lib):
+    # every point of a cell lies within b_max of its centre of mass, and the
+    # centre lies inside the cell, so sqrt(3)/2 s <= b_max <= sqrt(3) s: the
+    # rule at theta accepts whatever the pure test accepts at theta/sqrt(3) and
+    # nothing that it rejects at 2 theta/sqrt(3).  A rule that accepts more
+    # reaches fewer, coarser nodes, so per particle
+    #   count_pure(2 theta/sqrt(3)) <= count_bmax(theta) <= count_pure(theta/sqrt(3)),
+    # both strict for some particles (b_max is neither bound)
+    pm, _ = synth.plummer(2000, 23)
+    T = oracle.Tree(pm)
+    r3 = math.sqrt(3.0)
+    for theta in (0.5, 0.8):
+        _, _, c = T.accel(theta, 0.01, bmax=True)
+        _, _, c_hi = T.accel(2 * theta / r3, 0.01)
+        _, _, c_lo = T.accel(theta / r3, 0.01)
+        assert np.all(c_hi <= c) and np.all(c <= c_lo)
+        assert np.count_nonzero(c_hi < c) > 0 and np.count_nonzero(c < c_lo) > 0
+
+
+def test_bmax_rule_never_accepts_the_particles_own_cell(oracle_lib):
+    # d <= b_max for a particle inside the cell, so for theta <= 1 the rule
+    # never accepts a cell that holds the particle: the open-inside rule then
+    # changes nothing, while under the pure test it does at theta = 0.9, 1.0
+    pm, _ = synth.plummer(2000, 24)
+    T = oracle.Tree(pm)
+    for theta in (0.9, 1.0):
+        a0, p0, c0 = T.accel(theta, 0.01, bmax=True)
+        a1, p1, c1 = T.accel(theta, 0.01, bmax=True, open_inside=True)
+        assert np.array_equal(c0, c1) and np.array_equal(a0, a1) and np.array_equal(p0, p1)
+        _, _, d0 = T.accel(theta, 0.01)
+        _, _, d1 = T.accel(theta, 0.01, open_inside=True)
+        assert np.any(d0 != d1)
+

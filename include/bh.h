@@ -71,6 +71,16 @@ extern "C" {
                                  (second moments about the centre of mass,
                                  softened kernel expanded to second order);
                                  one particle per lane, Kahan sums required */
+#define BH_OPEN_BMAX    0x20u /* alternative size in the opening test
+                                 (Section V: other ways of computing the
+                                 criterion): a cell is accepted iff
+                                 b_max^2 < theta^2 d^2, b_max = distance from
+                                 its centre of mass to the farthest corner of
+                                 its cube, instead of s^2 < theta^2 d^2; for
+                                 theta <= 1 a cell holding the particle is then
+                                 never accepted.  The split walk (group 0) is
+                                 not available under it (a group-0 tuning runs
+                                 as group 1) */
 
 #define BH_MAX_DEPTH 21       /* levels below the root; fixed by the key width */
 

@@ -177,6 +177,9 @@ struct BuildBufs {
     // walk, two float4 per node: (xx, yy, zz, xy), (xz, yz, 0, 0)
     double *nodeI;
     float4 *nodeQ;
+    // b_max rule only (else null): FP64 b_max^2 per cell, the size that the
+    // rule puts in the opening test in place of the side
+    double *nodeB;
     unsigned node_cap;
     Small *small;
     int n_total;
@@ -212,6 +215,7 @@ struct WalkArgs {
     const float4 *nodeQ;  // quadrupole mode: 2 float4 per node (else null)
     const int4 *nodeR;
     const double4_32a *nodeD;
+    const double *nodeB;  // b_max rule: FP64 b_max^2 per cell (else null)
     const SysDyn *dyn;
     const float4 *spos;
     const uint32_t *sid;  // sorted -> virtual id

@@ -362,6 +362,44 @@ __device__ __forceinline__ int cell_end(const uint64_t *__restrict__ key, uint64
 
 __device__ __forceinline__ float pow2_neg(int l) { return __int_as_float((127 - l) << 23); }
 
+// b_max rule (BH_OPEN_BMAX): b_max^2 of a cell, the squared distance from its
+// centre of mass to the farthest corner of its cube.  Per axis the cube is
+// [c, c + s], c = lo + q s, s = side 2^-l, q the cell's integer position at
+// level l (the key prefix de-interleaved: bit 2 of each octal digit is x,
+// bit 1 y, bit 0 z); the farther face is max(com - c, (c + s) - com).  FP64,
+// every operation rounded on its own.
+__device__ __noinline__ double cell_bmax2(uint64_t key, int l, const SysDyn &D, double cx,
+                                          double cy, double cz)
+{
+    const uint64_t pre = key >> (3 * (kLevels - l));
+    unsigned q[3] = {0u, 0u, 0u};
+    for (int b = 0; b < l; ++b) {
+        const unsigned digit = (unsigned)(pre >> (3 * b)) & 7u;
+        q[0] |= ((digit >> 2) & 1u) << b;
+        q[1] |= ((digit >> 1) & 1u) << b;
+        q[2] |= (digit & 1u) << b;
+    }
+    const double s = __dmul_rn((double)D.side, __longlong_as_double((long long)(1023 - l) << 52));
+    const double com[3] = {cx, cy, cz};
+    double e2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double c = __dadd_rn((double)D.lo[a], __dmul_rn((double)q[a], s));
+        const double lo_gap = __dsub_rn(com[a], c);
+        const double hi_gap = __dsub_rn(__dadd_rn(c, s), com[a]);
+        const double e = lo_gap > hi_gap ? lo_gap : hi_gap;
+        e2 = __dadd_rn(e2, __dmul_rn(e, e));
+    }
+    return e2;
+}
+
+// The walk's FP32 threshold for b_max^2: accept iff d^2 > b_max^2 / theta^2,
+// rounded once; kept finite so that it never reads as the bucket marker.
+__device__ __forceinline__ float bmax_crit(double bm2, double theta2)
+{
+    return fminf(__double2float_rn(__ddiv_rn(bm2, theta2)), 3.40282347e38f);
+}
+
 // Writes every node that starts at a particle: skip pointer (the first node
 // starting at the cell's end particle), first, count, level and opening
 // threshold, plus its slot in its level's list.  The root's centre of mass
@@ -373,7 +411,7 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
              const uint32_t *__restrict__ noff, const float4 *__restrict__ spos,
              WNode *__restrict__ nodeW, int4 *__restrict__ nodeR, double4_32a *__restrict__ nodeD,
              uint32_t *__restrict__ nlist, double *__restrict__ nodeI, float4 *__restrict__ nodeQ,
-             Small *__restrict__ sm)
+             double *__restrict__ nodeB, Small *__restrict__ sm)
 {
     if (halted(sm)) return;
     __shared__ unsigned h[kNumLevels], base[kNumLevels];
@@ -420,7 +458,7 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
                 const float sl = __fmul_rn(D.side, pow2_neg(l));
                 crit = __fmul_rn(__fmul_rn(sl, sl), S.inv_theta2);
             }
-            nodeR[n] = make_int4(j, count, l, 0);
+            nodeR[n] = make_int4(j, count, l, c.x);
             // the walk's loop bound: every skip pointer lies past its node and
             // within the system's nodes (true by construction; checked here so
             // that the walk itself need not)
@@ -454,6 +492,11 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
                     const double cx = D.mx[0] / D.mtot, cy = D.mx[1] / D.mtot, cz = D.mx[2] / D.mtot;
                     const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
                     nodeW[n].a = make_float4(hx, hy, hz, (float)D.mtot);
+                    if (nodeB && crit != kBucketCrit) {
+                        const double bm2 = cell_bmax2(kj, 0, D, cx, cy, cz);
+                        nodeB[n] = bm2;
+                        crit = bmax_crit(bm2, S.theta2);
+                    }
                     nodeW[n].b = wn_pack(crit, (int)skip, cx, cy, cz, hx, hy, hz);
                     nodeD[n] = make_double4_32a(D.mtot, cx, cy, cz);
                 }
@@ -505,10 +548,19 @@ __device__ __noinline__ void second_moments(unsigned n, int4 C, float crit, int 
     nodeQ[2 * (size_t)n + 1] = make_float4((float)I[4], (float)I[5], 0.f, 0.f);
 }
 
+// b_max rule only (else nodeB is null): what the centre-of-mass pass needs to
+// rewrite a cell's threshold once its centre is known
+struct ComRule {
+    const SysStatic *sys;
+    const SysDyn *dyn;
+    const uint64_t *key;  // sorted keys
+    double *nodeB;        // FP64 b_max^2 per cell, read by the walk's tie test
+};
+
 __device__ __forceinline__ void com_node(unsigned n, const float4 *__restrict__ spos,
                                          WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR,
                                          double4_32a *__restrict__ nodeD, double *__restrict__ nodeI,
-                                         float4 *__restrict__ nodeQ)
+                                         float4 *__restrict__ nodeQ, const ComRule &R)
 {
     const int4 C = nodeR[n];  // first, count, level
     const uint4 B = nodeW[n].b;
@@ -538,7 +590,13 @@ __device__ __forceinline__ void com_node(unsigned n, const float4 *__restrict__ 
     const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
     nodeD[n] = make_double4_32a(M, cx, cy, cz);
     nodeW[n].a = make_float4(hx, hy, hz, (float)M);
-    nodeW[n].b = wn_pack(crit, skip, cx, cy, cz, hx, hy, hz);
+    float crit_w = crit;
+    if (R.nodeB && crit != kBucketCrit) {  // a cell (theta > 0): b_max threshold
+        const double bm2 = cell_bmax2(R.key[C.x], C.z, R.dyn[C.w], cx, cy, cz);
+        R.nodeB[n] = bm2;
+        crit_w = bmax_crit(bm2, R.sys[C.w].theta2);
+    }
+    nodeW[n].b = wn_pack(crit_w, skip, cx, cy, cz, hx, hy, hz);
     if (nodeI) second_moments(n, C, crit, skip, cx, cy, cz, spos, nodeW, nodeD, nodeI, nodeQ);
 }
 
@@ -546,13 +604,14 @@ __device__ __forceinline__ void com_node(unsigned n, const float4 *__restrict__ 
 __global__ void __launch_bounds__(256)
 k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
             WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4_32a *__restrict__ nodeD,
-            double *__restrict__ nodeI, float4 *__restrict__ nodeQ, const Small *__restrict__ sm)
+            double *__restrict__ nodeI, float4 *__restrict__ nodeQ, ComRule R,
+            const Small *__restrict__ sm)
 {
     if (halted(sm)) return;
     const unsigned cnt = sm->level_cnt[l];
     const unsigned off = sm->level_off[l];
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x)
-        com_node(nlist[off + k], spos, nodeW, nodeR, nodeD, nodeI, nodeQ);
+        com_node(nlist[off + k], spos, nodeW, nodeR, nodeD, nodeI, nodeQ, R);
 }
 
 // The deep levels l_hi .. l_lo, which hold few nodes, in one block: a block
@@ -560,14 +619,15 @@ k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict_
 __global__ void __launch_bounds__(1024)
 k_com_deep(int l_hi, int l_lo, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
            WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4_32a *__restrict__ nodeD,
-           double *__restrict__ nodeI, float4 *__restrict__ nodeQ, const Small *__restrict__ sm)
+           double *__restrict__ nodeI, float4 *__restrict__ nodeQ, ComRule R,
+           const Small *__restrict__ sm)
 {
     if (halted(sm)) return;
     for (int l = l_hi; l >= l_lo; --l) {
         const unsigned cnt = sm->level_cnt[l];
         const unsigned off = sm->level_off[l];
         for (unsigned k = threadIdx.x; k < cnt; k += blockDim.x)
-            com_node(nlist[off + k], spos, nodeW, nodeR, nodeD, nodeI, nodeQ);
+            com_node(nlist[off + k], spos, nodeW, nodeR, nodeD, nodeI, nodeQ, R);
         __syncthreads();
     }
 }
@@ -807,23 +867,24 @@ void launch_topology(const BuildBufs &b, cudaStream_t st)
     k_level_offsets<<<1, 32, 0, st>>>(b.small, b.noff, b.n_total, b.node_cap);
     k_topo_write<<<b.nchunks, kWideThreads, 0, st>>>(b.chunks, b.sys, b.dyn, b.key0, b.noff,
                                                       b.spos, b.nodeW, b.nodeR, b.nodeD, b.nlist,
-                                                      b.nodeI, b.nodeQ, b.small);
+                                                      b.nodeI, b.nodeQ, b.nodeB, b.small);
     g_launches += 2;
 }
 
 void launch_com(const BuildBufs &b, cudaStream_t st)
 {
     const int grid = b.nsm * 8;  // full occupancy: short per-thread chains of child loads
+    const ComRule R{b.sys, b.dyn, b.key0, b.nodeB};
     int l = kLevels;
     if (b.deep_cut <= kLevels) {
         k_com_deep<<<1, 1024, 0, st>>>(kLevels, b.deep_cut, b.nlist, b.spos, b.nodeW, b.nodeR,
-                                       b.nodeD, b.nodeI, b.nodeQ, b.small);
+                                       b.nodeD, b.nodeI, b.nodeQ, R, b.small);
         g_launches += 1;
         l = b.deep_cut - 1;
     }
     for (; l >= 1; --l) {
         k_com_level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeW, b.nodeR, b.nodeD,
-                                          b.nodeI, b.nodeQ, b.small);
+                                          b.nodeI, b.nodeQ, R, b.small);
         g_launches += 1;
     }
     if (b.nodeI) launch_root_moments(b, st);

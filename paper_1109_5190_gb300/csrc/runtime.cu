@@ -156,7 +156,7 @@ int download4(float *dst, const float4 *src, int64_t n, unsigned flags, cudaStre
 // ------------------------------------------------------- autotune cache
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, bh_tuning> g_tune_cache;
+std::map<std::tuple<int, int, int, int, unsigned>, bh_tuning> g_tune_cache;
 
 int log2_bucket(int64_t n)
 {
@@ -183,8 +183,8 @@ struct Forest {
     bool tables_dirty = true;
 
     DevBuf d_sys, d_dyn, d_chunks, d_mode, d_parts, key0, key1, val0, val1, rs_counts, scan_part,
-        spos, ncount, noff, nodeW, nodeR, nodeD, nlist, nodeI, nodeQ, d_small, d_diag_parts, d_diag_out,
-        d_counts, d_export;
+        spos, ncount, noff, nodeW, nodeR, nodeD, nlist, nodeI, nodeQ, nodeB, d_small, d_diag_parts,
+        d_diag_out, d_counts, d_export;
     unsigned node_cap = 0;
     struct TileSet {
         DevBuf buf;
@@ -292,6 +292,7 @@ struct Forest {
         b.nlist = nlist.as<uint32_t>();
         b.nodeI = quad() ? nodeI.as<double>() : nullptr;
         b.nodeQ = quad() ? nodeQ.as<float4>() : nullptr;
+        b.nodeB = bmax() ? nodeB.as<double>() : nullptr;
         b.node_cap = node_cap;
         b.small = small();
         b.n_total = n_total;
@@ -311,6 +312,7 @@ struct Forest {
             TRY(nodeI.ensure(cap * 6 * sizeof(double)));
             TRY(nodeQ.ensure(cap * 2 * sizeof(float4)));
         }
+        if (bmax()) TRY(nodeB.ensure(cap * sizeof(double)));
         node_cap = (unsigned)cap;
         invalidate_graph();
         return BH_OK;
@@ -450,6 +452,7 @@ struct Forest {
         a.nodeQ = quad() ? nodeQ.as<float4>() : nullptr;
         a.nodeR = nodeR.as<int4>();
         a.nodeD = nodeD.as<double4_32a>();
+        a.nodeB = bmax() ? nodeB.as<double>() : nullptr;
         a.dyn = d_dyn.as<SysDyn>();
         a.spos = spos.as<float4>();
         a.sid = val0.as<uint32_t>();
@@ -467,15 +470,21 @@ struct Forest {
     }
 
     // BH_OPEN_INSIDE and BH_QUADRUPOLE fix the shape to one particle per lane
-    WalkShape shape() const
+    WalkShape shape() const { return shape_of(tune); }
+    WalkShape shape_of(const bh_tuning &t) const
     {
         if (fixed_shape())
-            return WalkShape{1, tune.warps_per_block, tune.blocks_per_sm, 1, open_inside(), quad()};
-        return WalkShape{tune.ppl, tune.warps_per_block, tune.blocks_per_sm, tune.group, false,
+            return WalkShape{1, t.warps_per_block, t.blocks_per_sm, 1, open_inside(), quad()};
+        return WalkShape{t.ppl, t.warps_per_block, t.blocks_per_sm, walk_group(t.group), false,
                          false};
     }
+    // the split walk (group 0) recognises its top-level nodes by their
+    // threshold, a function of the level alone; under the b_max rule the
+    // threshold varies from cell to cell, so group 0 runs as group 1
+    int walk_group(int g) const { return fixed_shape() || (bmax() && g == 0) ? 1 : g; }
     bool open_inside() const { return (flags & BH_OPEN_INSIDE) != 0; }
     bool quad() const { return (flags & BH_QUADRUPOLE) != 0; }
+    bool bmax() const { return (flags & BH_OPEN_BMAX) != 0; }
     bool fixed_shape() const { return open_inside() || quad(); }
     bool kahan() const { return !(flags & BH_NO_KAHAN); }
     bool pot() const { return (flags & BH_POTENTIAL) != 0; }
@@ -704,7 +713,9 @@ struct Forest {
         double th = 0;
         for (auto *s : systems) th += s->theta;
         th /= std::max(1, nsys);
-        const auto key = std::make_tuple(dev, log2_bucket(n_total), (int)std::lround(th * 20), nsys > 1 ? 1 : 0);
+        const auto key = std::make_tuple(dev, log2_bucket(n_total), (int)std::lround(th * 20), nsys > 1 ? 1 : 0,
+                                         flags & (BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE |
+                                                  BH_QUADRUPOLE | BH_OPEN_BMAX));
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune_cache.find(key);
@@ -734,7 +745,8 @@ struct Forest {
                 for (int share : shares) {
                     bh_tuning t{p, w, 0, g, share};
                     if (fixed_shape() && (g != 1 || p != 1)) continue;
-                    WalkShape sh{p, w, 0, g, open_inside(), quad()};
+                    if (bmax() && g == 0) continue;
+                    const WalkShape sh = shape_of(t);
                     if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0) continue;
                     tune = t;  // walk_args reads the static share from tune
                     float ms_best = 1e30f;
@@ -782,10 +794,7 @@ struct Forest {
                                         "ppl 1/2, group 2, 0 or BH_GROUP_LIST with ppl 1; warps "
                                         "1..16; static_share 0..90; blocks_per_sm >= 0)");
         // the shape as it would be launched (BH_OPEN_INSIDE: one particle per lane)
-        const WalkShape sh =
-            fixed_shape()
-                ? WalkShape{1, t->warps_per_block, t->blocks_per_sm, 1, open_inside(), quad()}
-                : WalkShape{t->ppl, t->warps_per_block, t->blocks_per_sm, t->group, false, false};
+        const WalkShape sh = shape_of(*t);
         if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0)
             return fail(BH_ERR_INVALID, "walk shape does not fit on an SM");
         tune = *t;
@@ -811,7 +820,7 @@ struct Forest {
         TRY(ensure_tiles(1));
         TRY(clear_status());
         reset_step_counters();
-        WalkShape sh{1, 8, 0, fixed_shape() ? 1 : tune.group, open_inside(), quad()};
+        WalkShape sh{1, 8, 0, walk_group(tune.group), open_inside(), quad()};
         CKR(cudaMemsetAsync(small()->wstats, 0, sizeof(small()->wstats), st));
         launch_walk(walk_args(1, d_counts.as<uint32_t>()), sh, true, false, true, nsm, st);
         launches += 1;
@@ -940,7 +949,8 @@ static int check_bh_params(const bh_params *p)
     TRY(check_params(p->G, p->eps, p->theta));
     if (p->max_depth != BH_MAX_DEPTH) return fail(BH_ERR_INVALID, "max_depth must be 21");
     if (p->leaf_cap != 1) return fail(BH_ERR_INVALID, "leaf_cap must be 1");
-    if (p->flags & ~(BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE | BH_QUADRUPOLE))
+    if (p->flags &
+        ~(BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE | BH_QUADRUPOLE | BH_OPEN_BMAX))
         return fail(BH_ERR_INVALID, "unknown params flags");
     if ((p->flags & BH_QUADRUPOLE) && (p->flags & BH_NO_KAHAN))
         return fail(BH_ERR_INVALID, "BH_QUADRUPOLE needs Kahan sums");
@@ -1149,7 +1159,8 @@ int bh_forest_create(bh_forest **out, int nsys, const bh_system_desc *d, void *s
     if (!out) return fail(BH_ERR_INVALID, "null out");
     *out = nullptr;
     if (nsys < 1 || !d) return fail(BH_ERR_INVALID, "need at least one system");
-    if (flags & ~(BH_DEVICE_PTRS | BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE | BH_QUADRUPOLE))
+    if (flags & ~(BH_DEVICE_PTRS | BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE | BH_QUADRUPOLE |
+                  BH_OPEN_BMAX))
         return fail(BH_ERR_INVALID, "unknown flags");
     if ((flags & BH_QUADRUPOLE) && (flags & BH_NO_KAHAN))
         return fail(BH_ERR_INVALID, "BH_QUADRUPOLE needs Kahan sums");
@@ -1160,7 +1171,8 @@ int bh_forest_create(bh_forest **out, int nsys, const bh_system_desc *d, void *s
     std::unique_ptr<bh_forest> F(new (std::nothrow) bh_forest);
     if (!F) return fail(BH_ERR_OOM, "host allocation failed");
     Forest &f = F->f;
-    TRY(f.init(stream, flags & (BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE | BH_QUADRUPOLE)));
+    TRY(f.init(stream, flags & (BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE | BH_QUADRUPOLE |
+                                BH_OPEN_BMAX)));
     f.tune.static_share = nsys > 1 ? 0 : f.tune.static_share;  // uneven tiles: all dynamic
     TRY(f.begin_call());
     for (int s = 0; s < nsys; ++s) {
@@ -1300,11 +1312,13 @@ struct Job {
 // its share of the forest's scratch (two key and two id buffers, the sorted
 // copy, node counts and offsets) and of the node arrays (WNode 32 B, nodeR
 // 16 B, nodeD 32 B, level-list entry 4 B; up to ~2 nodes per particle with
-// the growth margin; in quadrupole mode also the second moments).
-size_t job_bytes(int64_t n, bool quad)
+// the growth margin; in quadrupole mode also the second moments, under the
+// b_max rule each cell's FP64 b_max^2).
+size_t job_bytes(int64_t n, unsigned flags)
 {
     const size_t per = 5 * 16 + (8 + 8 + 4 + 4 + 16 + 4 + 4) + 2 * (32 + 16 + 32 + 4) +
-                       (quad ? 2 * (6 * 8 + 2 * 16) : 0);  // second moments, FP64 + FP32
+                       ((flags & BH_QUADRUPOLE) ? 2 * (6 * 8 + 2 * 16) : 0) +  // FP64 + FP32
+                       ((flags & BH_OPEN_BMAX) ? 2 * 8 : 0);
     return (size_t)n * per + 4096 * 64;
 }
 
@@ -1475,7 +1489,7 @@ int bh_server_create(bh_server **out, size_t hbm_budget, int max_slots, void *st
     if (!out) return fail(BH_ERR_INVALID, "null out");
     *out = nullptr;
     if (max_slots < 1 || hbm_budget < (1u << 20)) return fail(BH_ERR_INVALID, "bad budget or slot count");
-    if (flags & ~(BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE | BH_QUADRUPOLE))
+    if (flags & ~(BH_POTENTIAL | BH_NO_KAHAN | BH_OPEN_INSIDE | BH_QUADRUPOLE | BH_OPEN_BMAX))
         return fail(BH_ERR_INVALID, "unknown flags");
     if ((flags & BH_QUADRUPOLE) && (flags & BH_NO_KAHAN))
         return fail(BH_ERR_INVALID, "BH_QUADRUPOLE needs Kahan sums");
@@ -1510,7 +1524,7 @@ int bh_submit(bh_server *s, const bh_request *r, uint64_t *ticket)
     j->n = r->n;
     j->G = r->G; j->eps = r->eps; j->theta = r->theta; j->dt = r->dt;
     j->nsteps = r->nsteps;
-    j->bytes = job_bytes(r->n, (s->flags & BH_QUADRUPOLE) != 0);
+    j->bytes = job_bytes(r->n, s->flags);
     if (j->bytes > s->budget) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stats.rejected++;

@@ -94,20 +94,26 @@ __device__ __forceinline__ void acc_fma(float &s, float &c, float a, float b)
 // its FP64 arithmetic) out of the walk loop.
 __device__ __noinline__ bool accept_fp64(const double4_32a *__restrict__ nodeD,
                                          const int4 *__restrict__ nodeR,
+                                         const double *__restrict__ nodeB,
                                          const SysStatic *__restrict__ sys,
                                          const SysDyn *__restrict__ dyn, int sysid, int node,
                                          float px, float py, float pz)
 {
-    const double side = (double)dyn[sysid].side;
     const double theta2 = sys[sysid].theta2;
-    const int level = nodeR[node].z;
     const double4_32a D = nodeD[node];
     const double dx = __dsub_rn(D.y, (double)px);
     const double dy = __dsub_rn(D.z, (double)py);
     const double dz = __dsub_rn(D.w, (double)pz);
     const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    const double s = side * __longlong_as_double((long long)(1023 - level) << 52);
-    return __dmul_rn(s, s) < __dmul_rn(theta2, d2);
+    double r2;  // the cell's size squared: b_max^2 under the b_max rule, else s^2
+    if (nodeB) {
+        r2 = nodeB[node];
+    } else {
+        const double s = (double)dyn[sysid].side *
+                         __longlong_as_double((long long)(1023 - nodeR[node].z) << 52);
+        r2 = __dmul_rn(s, s);
+    }
+    return r2 < __dmul_rn(theta2, d2);
 }
 
 // Offset within its tile of a lane's k-th particle.  When the whole warp
@@ -332,8 +338,8 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
                     const float diff = d2 - crit;
                     bool acc = diff > 0.f;
                     if (fabsf(diff) < band)
-                        acc = accept_fp64(a.nodeD, a.nodeR, a.sys, a.dyn, tl.sys, cur, px[k],
-                                          py[k], pz[k]);
+                        acc = accept_fp64(a.nodeD, a.nodeR, a.nodeB, a.sys, a.dyn, tl.sys, cur,
+                                          px[k], py[k], pz[k]);
                     // alternative rule: a cell holding the particle (its leaf lies in
                     // the cell's subtree, cur < leaf < skip) is always opened
                     if (OPEN && acc && crit >= 0.f && cur < leaf[k] && leaf[k] < skip) acc = false;
@@ -507,7 +513,8 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
                     const float diff = d2 - crit;
                     bool acc = diff > 0.f;
                     if (fabsf(diff) < band)
-                        acc = accept_fp64(a.nodeD, a.nodeR, a.sys, a.dyn, sysid, cur, px, py, pz);
+                        acc = accept_fp64(a.nodeD, a.nodeR, a.nodeB, a.sys, a.dyn, sysid, cur,
+                                          px, py, pz);
                     if (acc) {
                         const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[cur].x) == myj;
                         interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az,
@@ -561,7 +568,8 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
                     const float diff = d2 - crit;
                     bool acc = diff > 0.f;
                     if (fabsf(diff) < band)
-                        acc = accept_fp64(a.nodeD, a.nodeR, a.sys, a.dyn, sysid, n2, px, py, pz);
+                        acc = accept_fp64(a.nodeD, a.nodeR, a.nodeB, a.sys, a.dyn, sysid, n2,
+                                          px, py, pz);
                     if (acc) {
                         const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[n2].x) == myj;
                         interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az,
@@ -698,7 +706,8 @@ __global__ void __launch_bounds__(512, 3) k_walk_list(WalkArgs a)
                     const float diff = d2 - crit;
                     bool acc = diff > 0.f;
                     if (fabsf(diff) < band)
-                        acc = accept_fp64(a.nodeD, a.nodeR, a.sys, a.dyn, sysid, cur, px, py, pz);
+                        acc = accept_fp64(a.nodeD, a.nodeR, a.nodeB, a.sys, a.dyn, sysid, cur,
+                                          px, py, pz);
                     take = acc || crit == kBucketCrit;
                     nxt = take ? skip : cur + 1;
                 }

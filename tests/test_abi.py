@@ -51,6 +51,20 @@ def test_binding_wraps_every_symbol(lib):
     assert not unnamed, unnamed
 
 
+def test_binding_constants_match_the_header():
+    # every #define of include/bh.h with an integer value has the same value
+    # in the binding (status codes, flags, limits)
+    from paper_1109_5190_gb300 import binding as B
+    text = open(os.path.join(ROOT, "include", "bh.h")).read()
+    found = 0
+    for m in re.finditer(r"^#define\s+(BH_[A-Z0-9_]+)\s+\(?(-?(?:0x[0-9a-fA-F]+|\d+))u?\)?",
+                         text, flags=re.M):
+        name, val = m.group(1), int(m.group(2), 0)
+        assert getattr(B, name, None) == val, name
+        found += 1
+    assert found >= 20 and B.BH_OPEN_BMAX == 0x20
+
+
 def test_host_side_argument_errors(lib):
     from paper_1109_5190_gb300 import binding as B
     import numpy as np
@@ -70,6 +84,9 @@ def test_host_side_argument_errors(lib):
     assert B.lib.bh_create(ctypes.byref(h), ctypes.byref(p), 0, pm.ctypes.data, None, None, 0) \
         == B.BH_ERR_INVALID
     p.max_depth = 20
+    assert B.lib.bh_create(ctypes.byref(h), ctypes.byref(p), 4, pm.ctypes.data, None, None, 0) \
+        == B.BH_ERR_INVALID
+    p = B.params(flags=0x40)  # no such flag
     assert B.lib.bh_create(ctypes.byref(h), ctypes.byref(p), 4, pm.ctypes.data, None, None, 0) \
         == B.BH_ERR_INVALID
     assert B.lib.bh_step(None, 1, 1e-3, 0) == B.BH_ERR_INVALID

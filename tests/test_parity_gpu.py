@@ -519,6 +519,111 @@ def test_quadrupole_forest_and_error_against_direct_sum():
     assert errs[1] < 0.6 * errs[0], errs
 
 
+@pytest.mark.parametrize("kind,n,seed", [("plummer", 5000, 71), ("uniform", 6000, 72),
+                                         ("dups", 1000, 73)])
+@pytest.mark.parametrize("theta", [0.5, 0.8, 1.0])
+def test_bmax_rule_against_oracle(kind, n, seed, theta):
+    # BH_OPEN_BMAX: the cell's size in the opening test is b_max (centre of
+    # mass to the farthest corner of the cell); forces, potentials and exact
+    # interaction counts against the oracle under the same rule, then two KDK
+    # steps under it
+    pm, vel = gen(kind, n, seed)
+    h = make(pm, vel, 0.01, theta, flags=B.BH_POTENTIAL | B.BH_OPEN_BMAX)
+    try:
+        a = gpu_accel(h, n)
+        T = oracle.Tree(pm)
+        ref, pot, cnt = T.accel(theta, 0.01, bmax=True)
+        assert_accel_close(a, ref, what=f"bmax {kind} theta={theta}")
+        e = np.abs(a[:, 3] - pot) / np.abs(pot)
+        assert np.percentile(e, 99) <= 1e-5 and e.max() <= 1e-3
+        gc, _ = B.bh_interaction_count(h, n)
+        assert np.array_equal(gc.astype(np.int64), cnt)
+        _, _, cnt_pure = T.accel(theta, 0.01)
+        # sqrt(3)/2 s <= b_max <= sqrt(3) s: the rule opens more or fewer cells
+        # than the pure test, depending on how far centres sit from cell centres
+        assert np.any(cnt != cnt_pure)
+        B.bh_step(h, 2, 1e-3)
+        x = np.zeros_like(pm); a = np.zeros_like(pm)
+        B.bh_get_state(h, x, None, a)
+        ref, _, _ = oracle.Tree(x).accel(theta, 0.01, bmax=True)
+        assert_accel_close(a, ref, what=f"bmax {kind} theta={theta} step 2")
+    finally:
+        B.bh_destroy(h)
+
+
+def test_bmax_rule_every_shape_forest_and_options():
+    # under the rule every fused-walk shape and the interaction lists give
+    # bit-identical forces with the same counts, and a group-0 (split) tuning
+    # runs as group 1; the autotuner never picks the split walk; in a forest
+    # each system gets its own cells' b_max; the rule composes with the
+    # open-inside rule (which it makes redundant for theta <= 1) and with
+    # quadrupoles
+    n = 20000
+    pm, vel = synth.plummer(n, 74)
+    h = make(pm, vel, 0.01, 0.6, flags=B.BH_OPEN_BMAX)
+    try:
+        ref = cref = None
+        for group, ppl in ((1, 1), (1, 2), (1, 4), (2, 1), (4, 1), (8, 2), (32, 1), (32, 4),
+                           (B.BH_GROUP_LIST, 1), (0, 1)):
+            for w in (8, 16):
+                B.bh_set_tuning(h, ppl, w, 0, group, 75)
+                a = gpu_accel(h, n)
+                ref = a if ref is None else ref
+                assert np.array_equal(a, ref), (group, ppl, w)
+            c, _ = B.bh_interaction_count(h, n)
+            cref = c if cref is None else cref
+            assert np.array_equal(c, cref), (group, ppl)
+        _, _, cnt = oracle.Tree(pm).accel(0.6, 0.01, bmax=True)
+        assert np.array_equal(cref.astype(np.int64), cnt)
+        best = B.bh_autotune(h)
+        assert best[3] != 0
+        assert np.array_equal(gpu_accel(h, n), ref)
+    finally:
+        B.bh_destroy(h)
+    for extra in (B.BH_OPEN_INSIDE, B.BH_QUADRUPOLE):
+        h = make(pm, vel, 0.01, 0.9, flags=B.BH_OPEN_BMAX | extra)
+        try:
+            a = gpu_accel(h, n)
+            quad = extra == B.BH_QUADRUPOLE
+            ref, _, _ = oracle.Tree(pm).accel(0.9, 0.01, bmax=True, quadrupole=quad,
+                                              open_inside=not quad)
+            assert_accel_close(a, ref, what=f"bmax + {extra:#x}")
+        finally:
+            B.bh_destroy(h)
+    systems = synth.forest_systems(6, 256, 5000, seed=75, theta=0.6, eps=0.01)
+    descs = [dict(pos_mass=s.pos_mass, vel=s.vel, eps=0.01, theta=th, dt=1e-3)
+             for s, th in zip(systems, (0.5, 0.6, 0.7, 0.8, 0.9, 1.0))]
+    f = B.bh_forest_create(descs, flags=B.BH_OPEN_BMAX)
+    try:
+        B.bh_forest_compute_accel(f)
+        for k, d in enumerate(descs):
+            n = len(d["pos_mass"])
+            af = np.zeros((n, 4), np.float32)
+            B.bh_forest_get_state(f, k, None, None, af)
+            ref, _, _ = oracle.Tree(d["pos_mass"]).accel(d["theta"], 0.01, bmax=True)
+            assert_accel_close(af, ref, what=f"bmax forest system {k}")
+    finally:
+        B.bh_forest_destroy(f)
+
+
+@pytest.mark.parametrize("offset", [(1.0e3, -2.0e3, 5.0e2), (3.0e5, 0.0, -1.0e5)])
+def test_bmax_rule_far_from_the_origin(offset):
+    # the cells' corners lo + q s are formed in FP64 on both sides; a cloud far
+    # from the origin checks them where FP32 keeps few bits of the shape
+    pm, vel = synth.plummer(6000, 76)
+    pm = pm.copy()
+    pm[:, :3] += np.asarray(offset, np.float32)
+    h = make(pm, vel, 0.01, 0.7, flags=B.BH_OPEN_BMAX)
+    try:
+        a = gpu_accel(h, 6000)
+        ref, _, cnt = oracle.Tree(pm).accel(0.7, 0.01, bmax=True)
+        assert_accel_close(a, ref, what=f"bmax offset {offset}")
+        gc, _ = B.bh_interaction_count(h, 6000)
+        assert np.array_equal(gc.astype(np.int64), cnt)
+    finally:
+        B.bh_destroy(h)
+
+
 @pytest.mark.parametrize("offset", [(1.0e3, -2.0e3, 5.0e2), (3.0e5, 0.0, -1.0e5)])
 def test_system_far_from_the_origin(offset):
     # a Plummer sphere moved far from the origin: FP32 coordinates keep fewer

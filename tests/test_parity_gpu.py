@@ -606,6 +606,81 @@ def test_bmax_rule_every_shape_forest_and_options():
         B.bh_forest_destroy(f)
 
 
+def test_checkpoint_resume_is_bit_exact():
+    # the state bh_get_state returns is a checkpoint: a new system created from
+    # it, or an existing one given it with bh_set_state (with or without the
+    # stored acceleration), continues with exactly the steps the original
+    # system takes from there
+    n = 20000
+    pm, vel = synth.plummer(n, 78)
+
+    def state(h):
+        x = np.zeros_like(pm); v = np.zeros_like(pm); a = np.zeros_like(pm)
+        B.bh_get_state(h, x, v, a)
+        return x, v, a
+
+    h = make(pm, vel, 0.01, 0.6)
+    try:
+        B.bh_step(h, 3, 1e-3)
+        ck = state(h)
+        B.bh_step(h, 3, 1e-3, True)
+        want = state(h)
+    finally:
+        B.bh_destroy(h)
+    for route in ("create", "set_state", "set_state+acc"):
+        if route == "create":
+            h = make(ck[0], ck[1], 0.01, 0.6)
+        else:
+            h = make(pm, None, 0.01, 0.6)
+            B.bh_step(h, 1, 1e-3)  # some other state first
+            B.bh_set_state(h, ck[0], ck[1], ck[2] if route == "set_state+acc" else None)
+        try:
+            B.bh_step(h, 3, 1e-3)
+            got = state(h)
+        finally:
+            B.bh_destroy(h)
+        for g, w in zip(got, want):
+            assert np.array_equal(g, w), route
+
+
+def test_bmax_rule_theta_zero_and_served():
+    # theta = 0 never accepts under either rule: the walk is the direct sum,
+    # bit-identical with and without the rule; and a server created with the
+    # rule gives every request the result it gets alone under the rule
+    pm, vel = synth.plummer(4096, 77)
+    outs = []
+    for fl in (0, B.BH_OPEN_BMAX):
+        h = make(pm, vel, 0.01, 0.0, flags=fl)
+        try:
+            outs.append(gpu_accel(h, 4096))
+            _, tot = B.bh_interaction_count(h, 4096)
+            assert tot == 4096 * 4096
+        finally:
+            B.bh_destroy(h)
+    assert np.array_equal(outs[0], outs[1])
+    ref, _ = oracle.direct(pm, 0.01)
+    assert_accel_close(outs[1], ref, what="bmax theta=0 vs direct")
+    reqs = [(synth.plummer if k % 2 else synth.uniform_cube)(2000 + 900 * k, 110 + k)
+            for k in range(5)]
+    srv = B.bh_server_create(4 << 30, 3, flags=B.BH_OPEN_BMAX)
+    try:
+        tickets = [B.bh_submit(srv, pm, v, 1.0, 0.01, 0.6 + 0.05 * k, 1e-3, 2 + k)
+                   for k, (pm, v) in enumerate(reqs)]
+        res = [B.bh_wait(srv, t, len(pm), 120.0) for t, (pm, v) in zip(tickets, reqs)]
+    finally:
+        B.bh_server_destroy(srv)
+    for k, ((pm, v), out) in enumerate(zip(reqs, res)):
+        assert out["status"] == 0 and out["steps_done"] == 2 + k
+        h = make(pm, v, 0.01, 0.6 + 0.05 * k, flags=B.BH_OPEN_BMAX)
+        try:
+            B.bh_step(h, 2 + k, 1e-3)
+            x = np.zeros_like(pm); a = np.zeros_like(pm)
+            B.bh_get_state(h, x, None, a)
+        finally:
+            B.bh_destroy(h)
+        assert np.array_equal(out["pos_mass"], x) and np.array_equal(out["acc"], a)
+
+
 @pytest.mark.parametrize("offset", [(1.0e3, -2.0e3, 5.0e2), (3.0e5, 0.0, -1.0e5)])
 def test_bmax_rule_far_from_the_origin(offset):
     # the cells' corners lo + q s are formed in FP64 on both sides; a cloud far

@@ -198,11 +198,15 @@ k_rs_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
 
 // ---------------------------------------------------------------- scan
 
+// Tile sums part[b] of the input; also clears zero[0..nzero) (the next
+// radix pass's count buffer), which saves the stream a separate memset.
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_reduce(const uint32_t *__restrict__ in, int n, uint32_t *__restrict__ part,
-              const int *__restrict__ status)
+              uint32_t *__restrict__ zero, int nzero, const int *__restrict__ status)
 {
     if (status && *status) return;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nzero; q += gridDim.x * blockDim.x)
+        zero[q] = 0u;
     const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     uint32_t s = 0;
 #pragma unroll
@@ -213,7 +217,8 @@ k_scan_reduce(const uint32_t *__restrict__ in, int n, uint32_t *__restrict__ par
     if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-// Scans part[0..nb) in place (exclusive); *total = sum.
+// Scans part[0..nb) in place (exclusive); *total = sum.  Used when there are
+// more tiles than k_scan_apply adds up inline.
 __global__ void __launch_bounds__(1024)
 k_scan_part(uint32_t *__restrict__ part, int nb, uint32_t *__restrict__ total,
             const int *__restrict__ status)
@@ -241,11 +246,27 @@ k_scan_part(uint32_t *__restrict__ part, int nb, uint32_t *__restrict__ total,
     if (threadIdx.x == 0 && total) *total = carry;
 }
 
+// Up to this many tiles, each k_scan_apply block adds up the tile sums before
+// its own (one load per thread), so no separate pass scans them.
+constexpr int kScanInlineTiles = kScanThreads;
+
+// Scans tile b.  inline_part: part[] holds raw tile sums and the block adds
+// up those before it, and the last block writes the grand total to *total
+// (if given); otherwise part[] was scanned by k_scan_part.
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_apply(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n,
-             const uint32_t *__restrict__ part, const int *__restrict__ status)
+             const uint32_t *__restrict__ part, int inline_part, uint32_t *__restrict__ total,
+             const int *__restrict__ status)
 {
     if (status && *status) return;
+    uint32_t offset;
+    if (inline_part) {
+        uint32_t before = 0;
+        for (int q = threadIdx.x; q < (int)blockIdx.x; q += blockDim.x) before += part[q];
+        block_exclusive(before, &offset);
+    } else {
+        offset = part[blockIdx.x];
+    }
     const int base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     uint32_t x[kScanItems], s = 0;
 #pragma unroll
@@ -254,12 +275,14 @@ k_scan_apply(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n,
         s += x[q];
     }
     uint32_t tot;
-    uint32_t e = block_exclusive(s, &tot) + part[blockIdx.x];
+    uint32_t e = block_exclusive(s, &tot) + offset;
 #pragma unroll
     for (int q = 0; q < kScanItems; ++q) {
         if (base + q < n) out[base + q] = e;
         e += x[q];
     }
+    if (inline_part && total && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0)
+        *total = offset + tot;
 }
 
 // One block scans up to kScanSingleMax values: rows of 4096 (4 per thread,
@@ -294,20 +317,37 @@ k_scan_single(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int n
 
 }  // namespace
 
-void launch_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *partials, uint32_t *total,
-                 const int *status, cudaStream_t st)
+namespace {
+
+// launch_scan, and also clears zero[0..nzero) on the way
+void scan_and_clear(const uint32_t *in, uint32_t *out, int n, uint32_t *partials,
+                    uint32_t *total, const int *status, cudaStream_t st, uint32_t *zero,
+                    int nzero)
 {
     if (n <= 0) return;
     if (n <= kScanSingleMax) {
+        if (nzero > 0) cudaMemsetAsync(zero, 0, sizeof(uint32_t) * (size_t)nzero, st);
         k_scan_single<<<1, 1024, 0, st>>>(in, out, n, total, status);
         g_launches += 1;
         return;
     }
     const int nb = (n + kScanTile - 1) / kScanTile;
-    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, n, partials, status);
-    k_scan_part<<<1, 1024, 0, st>>>(partials, nb, total, status);
-    k_scan_apply<<<nb, kScanThreads, 0, st>>>(in, out, n, partials, status);
-    g_launches += 3;
+    const int inline_part = nb <= kScanInlineTiles;
+    k_scan_reduce<<<nb, kScanThreads, 0, st>>>(in, n, partials, zero, nzero, status);
+    if (!inline_part) {
+        k_scan_part<<<1, 1024, 0, st>>>(partials, nb, total, status);
+        g_launches += 1;
+    }
+    k_scan_apply<<<nb, kScanThreads, 0, st>>>(in, out, n, partials, inline_part, total, status);
+    g_launches += 2;
+}
+
+}  // namespace
+
+void launch_scan(const uint32_t *in, uint32_t *out, int n, uint32_t *partials, uint32_t *total,
+                 const int *status, cudaStream_t st)
+{
+    scan_and_clear(in, out, n, partials, total, status, st, nullptr, 0);
 }
 
 // Opts the scatter in to more than 48 KiB of dynamic shared memory; called
@@ -331,8 +371,9 @@ void launch_sort(const BuildBufs &b, cudaStream_t st)
     for (int pass = 0; pass < kRadixPasses; ++pass) {
         const int shift = pass * kRadixBits;
         const bool more = pass + 1 < kRadixPasses;
-        launch_scan(cur, cur, ncounts, b.scan_part, nullptr, &b.small->status, st);
-        if (more) cudaMemsetAsync(nxt, 0, sizeof(uint32_t) * (size_t)ncounts, st);
+        // the scan also clears the count buffer this pass's scatter fills
+        scan_and_clear(cur, cur, ncounts, b.scan_part, nullptr, &b.small->status, st, nxt,
+                       more ? ncounts : 0);
         k_rs_scatter<<<b.nchunks, kSortThreads, kScatterSmem, st>>>(
             kin, vin, kout, vout, b.chunks, b.sys, cur, shift, more ? nxt : nullptr, b.small);
         g_launches += 1;

@@ -587,7 +587,9 @@ def main():
     ap.add_argument("--ppl", type=int, default=0, help="fix the walk shape (skip the autotuner)")
     ap.add_argument("--warps", type=int, default=8)
     ap.add_argument("--group", type=int, default=1,
-                    help="lanes voting together (1, 2, 4, 8 or 32; 0 = split walk)")
+                    help="lanes voting together (1, 2, 4, 8 or 32; 0 = split walk, "
+                         "64 = interaction lists, 65 = one lane per particle over "
+                         "sibling-ordered node records)")
     ap.add_argument("--no-kahan", action="store_true", help="plain FP32 force sums")
     ap.add_argument("--static-share", type=int, default=75)
     ap.add_argument("--no-graph", action="store_true", help="launch each step's kernels directly")

@@ -133,13 +133,20 @@ typedef struct bh_node {
  *                   BH_GROUP_LIST (64) = interaction lists (ppl 1): the warp
  *                   walks the union of its tile's traversals into a list of
  *                   (node, lanes that take it), then evaluates the list.
+ *                   BH_GROUP_SIBLINGS (65) = one lane per particle (ppl 1,
+ *                   no vote) over a copy of the node records built after each
+ *                   tree in which every node's children sit next to each
+ *                   other, so lanes at sibling nodes share cache lines.  Not
+ *                   available with BH_OPEN_INSIDE, BH_QUADRUPOLE or
+ *                   BH_OPEN_BMAX (it runs as group 1 there).
  * Accelerations are bit-identical for every shape with group >= 1 (the
- * interaction lists included).  The split
+ * interaction lists and the sibling-order walk included).  The split
  * walk sums the same terms in another order, fixed by each particle's tile (32
  * consecutive sorted particles of its system), so its results are
  * bit-identical among split shapes, alone or in a forest, and differ from the
  * others only by rounding; interaction counts are the same for every shape. */
 #define BH_GROUP_LIST 64
+#define BH_GROUP_SIBLINGS 65
 
 typedef struct bh_tuning {
     int ppl;

@@ -23,6 +23,7 @@ lib = C.CDLL(_LIB_PATH)
 
 BH_OK, BH_PENDING = 0, 1
 BH_GROUP_LIST = 64  # bh_tuning.group: interaction-list walk
+BH_GROUP_SIBLINGS = 65  # bh_tuning.group: one lane per particle over sibling-ordered nodes
 BH_ERR_INVALID, BH_ERR_OOM, BH_ERR_BUDGET, BH_ERR_CAPACITY = -1, -2, -3, -4
 BH_ERR_TIMEOUT, BH_ERR_CUDA, BH_ERR_STATE, BH_ERR_CANCELLED = -5, -6, -7, -8
 BH_DEVICE_PTRS, BH_POTENTIAL, BH_NO_KAHAN, BH_OPEN_INSIDE, BH_QUADRUPOLE = 0x1, 0x2, 0x4, 0x8, 0x10

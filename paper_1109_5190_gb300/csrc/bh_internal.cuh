@@ -108,11 +108,28 @@ struct Small {
 //       the next node after the subtree (> the node's own index); the low part com - h of each
 //       coordinate as an int16 multiple of 2^(e - 127) (e chosen per node
 //       from the largest |h|, so the low part keeps 2^-16 of an FP32 ulp).
-// Fields the walk rarely needs live in nodeR = (first, count, level, 0).
+// Fields the walk rarely needs live in nodeR = (first, count, level, system).
 struct __align__(32) WNode {
     float4 a;
     uint4 b;
 };
+
+// Sibling-order copy of the records (walk shape BH_GROUP_SIBLINGS): system s's
+// root at index s, then the children of every node next to each other, the
+// blocks in the depth-first order of their parents.  The walk gets these
+// records as WalkArgs::nodeW and a sibling-order copy of the FP64 centres of
+// mass as WalkArgs::nodeD.
+// Same 32 bytes, same a, lo parts and exponent; b differs:
+//   b = (target, next, lo_xy, lo_z | level << 16 | kind << 21 | e << 23)
+//   kind kLvlCell: target = sibling-order index of the first child; the
+//       threshold is s^2/theta^2 from the level, as the topology pass forms it;
+//   kind kLvlLeaf: target = the particle (sorted index);
+//   kind kLvlBucket (a depth-cap bucket, or any cell when theta = 0):
+//       target = the node's depth-first index (its members are in nodeR);
+//   next = sibling-order index of the node after the subtree in depth-first
+//       order, or kLvlEnd after the system's last node.
+constexpr unsigned kLvlCell = 0, kLvlLeaf = 1, kLvlBucket = 2;
+constexpr unsigned kLvlEnd = 0xffffffffu;
 
 #ifdef __CUDACC__
 __device__ __forceinline__ float wn_crit(const uint4 &b) { return __uint_as_float(b.x); }
@@ -180,6 +197,12 @@ struct BuildBufs {
     // b_max rule only (else null): FP64 b_max^2 per cell, the size that the
     // rule puts in the opening test in place of the side
     double *nodeB;
+    // sibling-order walk only (else null): the sibling-order records and FP64
+    // centres of mass, the maps depth-first -> sibling order (lidx) and back
+    // (ldfs), and per-node child counts (node_cap entries, scanned in place)
+    WNode *nodeF;
+    double4_32a *nodeDF;
+    uint32_t *lidx, *ldfs, *sib_count;
     unsigned node_cap;
     Small *small;
     int n_total;
@@ -197,6 +220,7 @@ void launch_permute(const BuildBufs &b, cudaStream_t st);
 void launch_topology(const BuildBufs &b, cudaStream_t st);
 void launch_com(const BuildBufs &b, cudaStream_t st);
 void launch_root_moments(const BuildBufs &b, cudaStream_t st);  // quadrupole mode
+void launch_sibling_order(const BuildBufs &b, cudaStream_t st);  // sibling-order walk
 void launch_kick(const BuildBufs &b, cudaStream_t st);
 void launch_restore(const BuildBufs &b, cudaStream_t st);
 void launch_validate(const BuildBufs &b, cudaStream_t st);

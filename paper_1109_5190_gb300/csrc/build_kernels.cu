@@ -651,6 +651,117 @@ __global__ void k_root_moments(const SysStatic *__restrict__ sys,
     second_moments(n, C, wn_crit(B), wn_skip(B), D.y, D.z, D.w, spos, nodeW, nodeD, nodeI, nodeQ);
 }
 
+// ----------------------------------------------- sibling-order copy (walk)
+//
+// For the sibling-order walk: every system's root at the system's index, then
+// the children of each node stored next to each other, the blocks in the
+// depth-first order of their parents (position of child r of node p:
+// nsys + (children of the nodes before p) + r).  Child counts and positions
+// come from each cell's chain of children (first child p + 1, then skip
+// pointers up to p's own skip); then the records are rewritten with
+// sibling-order pointers.  Each particle's walk visits the same nodes in the
+// same order as in depth-first order; only where the records sit changes.
+
+// A node has children iff it holds two or more particles above the depth cap.
+__device__ __forceinline__ bool has_children(const int4 &R) { return R.y > 1 && R.z < kLevels; }
+
+// nch[k] = children of node k (0 for leaves and buckets), for every k below
+// the node capacity (0 past the last node), for the scan that follows.
+__global__ void __launch_bounds__(256)
+k_sib_count(const uint32_t *__restrict__ mtot, unsigned cap, const WNode *__restrict__ nodeW,
+            const int4 *__restrict__ nodeR, uint32_t *__restrict__ nch,
+            const Small *__restrict__ sm)
+{
+    if (halted(sm)) return;
+    const unsigned m = *mtot;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cap; k += gridDim.x * blockDim.x) {
+        unsigned c = 0;
+        if (k < m && has_children(nodeR[k])) {
+            const unsigned end = (unsigned)wn_skip(nodeW[k].b);
+            for (unsigned ch = k + 1; ch < end; ch = (unsigned)wn_skip(nodeW[ch].b)) ++c;
+        }
+        nch[k] = c;
+    }
+}
+
+// Places every node: roots at their system's index, the children of node p at
+// nsys + excl[p] + r (excl = exclusive scan of nch).  lidx: depth-first ->
+// sibling order; ldfs: the inverse.
+__global__ void __launch_bounds__(256)
+k_sib_place(const uint32_t *__restrict__ mtot, int nsys, const WNode *__restrict__ nodeW,
+            const int4 *__restrict__ nodeR, const uint32_t *__restrict__ excl,
+            uint32_t *__restrict__ lidx, uint32_t *__restrict__ ldfs,
+            const Small *__restrict__ sm)
+{
+    if (halted(sm)) return;
+    const unsigned m = *mtot;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        const int4 R = nodeR[k];
+        if (R.z == 0) {
+            lidx[k] = (unsigned)R.w;
+            ldfs[R.w] = k;
+        }
+        if (!has_children(R)) continue;
+        const unsigned end = (unsigned)wn_skip(nodeW[k].b);
+        unsigned pos = (unsigned)nsys + excl[k];
+        for (unsigned ch = k + 1; ch < end; ch = (unsigned)wn_skip(nodeW[ch].b), ++pos) {
+            lidx[ch] = pos;
+            ldfs[pos] = ch;
+        }
+    }
+}
+
+// Rewrites node k's record at its sibling-order slot.  Checks that the map is
+// a bijection (ldfs[lidx[k]] == k with lidx[k] < m for every k): then the
+// sibling-order pointers copy the depth-first ones one to one, and the walk
+// over them visits what the depth-first walk visits and ends where it ends.
+__global__ void __launch_bounds__(256)
+k_sib_write(const SysStatic *__restrict__ sys, const uint32_t *__restrict__ noff, int n_total,
+            const WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR,
+            const double4_32a *__restrict__ nodeD, const uint32_t *__restrict__ lidx,
+            const uint32_t *__restrict__ ldfs, WNode *__restrict__ nodeF,
+            double4_32a *__restrict__ nodeDF, Small *__restrict__ sm)
+{
+    if (halted(sm)) return;
+    const unsigned m = noff[n_total];
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        const unsigned me = lidx[k];
+        const int4 R = nodeR[k];  // first, count, level, system
+        // a bijection, with every system's root at the system's index
+        if (me >= m || ldfs[me] != k || (R.z == 0 && me != (unsigned)R.w)) {
+            atomicExch(&sm->status, ST_WALK_LIMIT);
+            return;
+        }
+        const WNode W = nodeW[k];
+        const float crit = wn_crit(W.b);
+        const unsigned skip = (unsigned)wn_skip(W.b);
+        const SysStatic &S = sys[R.w];
+        const unsigned nend = noff[S.start + S.n];
+        unsigned kind, target;
+        if (crit == kLeafCrit) {
+            kind = kLvlLeaf;
+            target = (unsigned)R.x;
+        } else if (crit == kBucketCrit) {
+            kind = kLvlBucket;
+            target = k;
+        } else {
+            if (k + 1 >= nend) {  // a cell has children (true by construction)
+                atomicExch(&sm->status, ST_WALK_LIMIT);
+                return;
+            }
+            kind = kLvlCell;
+            target = lidx[k + 1];  // first child: the next node in depth-first order
+        }
+        const unsigned next = skip < nend ? lidx[skip] : kLvlEnd;
+        const unsigned meta = (W.b.w & 0xff80ffffu) | ((unsigned)R.z << 16) | (kind << 21);
+        WNode F;
+        F.a = W.a;
+        F.b = make_uint4(target, next, W.b.z, meta);
+        nodeF[me] = F;
+        nodeDF[me] = nodeD[k];
+    }
+}
+
 // ------------------------------------------------------ closing kick (A8)
 
 __global__ void __launch_bounds__(kWideThreads)
@@ -895,6 +1006,20 @@ void launch_root_moments(const BuildBufs &b, cudaStream_t st)
     k_root_moments<<<b.nsys, 32, 0, st>>>(b.sys, b.noff, b.spos, b.nodeW, b.nodeR, b.nodeD,
                                            b.nodeI, b.nodeQ, b.small);
     g_launches += 1;
+}
+
+void launch_sibling_order(const BuildBufs &b, cudaStream_t st)
+{
+    const uint32_t *mtot = b.noff + b.n_total;
+    const int grid = b.nsm * 8;
+    k_sib_count<<<grid, 256, 0, st>>>(mtot, b.node_cap, b.nodeW, b.nodeR, b.sib_count, b.small);
+    launch_scan(b.sib_count, b.sib_count, (int)b.node_cap, b.scan_part, nullptr,
+                &b.small->status, st);
+    k_sib_place<<<grid, 256, 0, st>>>(mtot, b.nsys, b.nodeW, b.nodeR, b.sib_count, b.lidx,
+                                      b.ldfs, b.small);
+    k_sib_write<<<grid, 256, 0, st>>>(b.sys, b.noff, b.n_total, b.nodeW, b.nodeR, b.nodeD,
+                                      b.lidx, b.ldfs, b.nodeF, b.nodeDF, b.small);
+    g_launches += 3;
 }
 
 void launch_kick(const BuildBufs &b, cudaStream_t st)

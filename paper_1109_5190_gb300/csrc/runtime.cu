@@ -183,8 +183,8 @@ struct Forest {
     bool tables_dirty = true;
 
     DevBuf d_sys, d_dyn, d_chunks, d_mode, d_parts, key0, key1, val0, val1, rs_counts, scan_part,
-        spos, ncount, noff, nodeW, nodeR, nodeD, nlist, nodeI, nodeQ, nodeB, d_small, d_diag_parts,
-        d_diag_out, d_counts, d_export;
+        spos, ncount, noff, nodeW, nodeR, nodeD, nlist, nodeI, nodeQ, nodeB, nodeF, nodeDF, lidx,
+        ldfs, sib_count, d_small, d_diag_parts, d_diag_out, d_counts, d_export;
     unsigned node_cap = 0;
     struct TileSet {
         DevBuf buf;
@@ -293,6 +293,12 @@ struct Forest {
         b.nodeI = quad() ? nodeI.as<double>() : nullptr;
         b.nodeQ = quad() ? nodeQ.as<float4>() : nullptr;
         b.nodeB = bmax() ? nodeB.as<double>() : nullptr;
+        const bool lvl = sib_walk() && nodeF.p;
+        b.nodeF = lvl ? nodeF.as<WNode>() : nullptr;
+        b.nodeDF = lvl ? nodeDF.as<double4_32a>() : nullptr;
+        b.lidx = lvl ? lidx.as<uint32_t>() : nullptr;
+        b.ldfs = lvl ? ldfs.as<uint32_t>() : nullptr;
+        b.sib_count = lvl ? sib_count.as<uint32_t>() : nullptr;
         b.node_cap = node_cap;
         b.small = small();
         b.n_total = n_total;
@@ -315,6 +321,26 @@ struct Forest {
         if (bmax()) TRY(nodeB.ensure(cap * sizeof(double)));
         node_cap = (unsigned)cap;
         invalidate_graph();
+        return BH_OK;
+    }
+
+    // Buffers of the sibling-order walk, sized for the node capacity (the
+    // child-count scan runs over all of it, so its partials too); allocated
+    // only while that walk is the tuned shape, and never during a capture.
+    int ensure_sib_bufs()
+    {
+        if (!sib_walk()) return BH_OK;
+        const size_t cap = node_cap;
+        const size_t want[6] = {cap * sizeof(WNode), cap * sizeof(double4_32a), cap * 4, cap * 4,
+                                cap * 4, ((cap + kScanTile - 1) / kScanTile + 1) * 4};
+        DevBuf *bufs4[6] = {&nodeF, &nodeDF, &lidx, &ldfs, &sib_count, &scan_part};
+        bool moved = false;
+        for (int q = 0; q < 6; ++q) {
+            if (bufs4[q]->p && bufs4[q]->bytes >= want[q]) continue;
+            TRY(bufs4[q]->ensure(want[q]));
+            moved = true;
+        }
+        if (moved) invalidate_graph();
         return BH_OK;
     }
 
@@ -453,6 +479,11 @@ struct Forest {
         a.nodeR = nodeR.as<int4>();
         a.nodeD = nodeD.as<double4_32a>();
         a.nodeB = bmax() ? nodeB.as<double>() : nullptr;
+        // the sibling-order walk reads the sibling-order copies in their place
+        if (sib_walk() && nodeF.p) {
+            a.nodeW = nodeF.as<WNode>();
+            a.nodeD = nodeDF.as<double4_32a>();
+        }
         a.dyn = d_dyn.as<SysDyn>();
         a.spos = spos.as<float4>();
         a.sid = val0.as<uint32_t>();
@@ -479,9 +510,14 @@ struct Forest {
                          false};
     }
     // the split walk (group 0) recognises its top-level nodes by their
-    // threshold, a function of the level alone; under the b_max rule the
-    // threshold varies from cell to cell, so group 0 runs as group 1
-    int walk_group(int g) const { return fixed_shape() || (bmax() && g == 0) ? 1 : g; }
+    // threshold, and the sibling-order walk forms it from the level: both need
+    // it to be a function of the level alone, which under the b_max rule it
+    // is not, so there they run as group 1
+    int walk_group(int g) const
+    {
+        return fixed_shape() || (bmax() && (g == 0 || g == BH_GROUP_SIBLINGS)) ? 1 : g;
+    }
+    bool sib_walk() const { return shape().group == BH_GROUP_SIBLINGS; }
     bool open_inside() const { return (flags & BH_OPEN_INSIDE) != 0; }
     bool quad() const { return (flags & BH_QUADRUPOLE) != 0; }
     bool bmax() const { return (flags & BH_OPEN_BMAX) != 0; }
@@ -548,6 +584,10 @@ struct Forest {
         launch_permute(b, st);
         launch_topology(b, st);
         launch_com(b, st);
+        if (sib_walk()) {
+            if (!b.nodeF) return fail(BH_ERR_STATE, "sibling-order buffers missing");
+            launch_sibling_order(b, st);
+        }
         m[2] = mark();
         if (do_walk &&
             launch_walk(walk_args(tune.ppl, nullptr), shape(), kahan(), pot(), false, nsm, st) < 0)
@@ -615,6 +655,7 @@ struct Forest {
             if (attempt > 8) return fail(BH_ERR_CAPACITY, "node buffer kept overflowing");
             TRY(clear_status());
             TRY(ensure_tiles(tune.ppl));
+            TRY(ensure_sib_bufs());
             if (graph) {
                 walk_max_blocks_per_sm(shape(), kahan(), pot());  // occupancy query outside capture
                 if (!gexec || g_nsteps != remaining || g_cap != node_cap || g_ntotal != n_total ||
@@ -729,7 +770,11 @@ struct Forest {
         // (group, particles per lane) candidates x warps per block
         // (the interaction-list walk is left out: measured 2-2.5x slower than
         // the fused walks on every workload tried, it would only lengthen tuning)
-        const int shapes[10][2] = {{0, 1}, {1, 1}, {1, 2}, {1, 4}, {2, 1}, {4, 1}, {8, 1}, {32, 1}, {32, 2}, {32, 4}};
+        // (the sibling-order walk is left out too: slower than one lane per
+        // particle in depth-first order on every workload measured, and its
+        // copy adds build time the walk-only timing here would not see)
+        const int shapes[10][2] = {{0, 1}, {1, 1}, {1, 2}, {1, 4}, {2, 1}, {4, 1}, {8, 1}, {32, 1},
+                                   {32, 2}, {32, 4}};
         const int warps[2] = {8, 16};
         cudaEvent_t e0, e1;
         CKR(cudaEventCreate(&e0));
@@ -786,13 +831,15 @@ struct Forest {
             t->warps_per_block > 32 || t->blocks_per_sm < 0 ||
             t->warps_per_block > 16 ||
             (t->group != 0 && t->group != 1 && t->group != 2 && t->group != 4 && t->group != 8 &&
-             t->group != 32 && t->group != BH_GROUP_LIST) ||
+             t->group != 32 && t->group != BH_GROUP_LIST && t->group != BH_GROUP_SIBLINGS) ||
             t->static_share < 0 || t->static_share > 90 ||
             (t->group != 32 && t->group != 1 && t->ppl == 4) ||
-            ((t->group == 2 || t->group == 0 || t->group == BH_GROUP_LIST) && t->ppl != 1))
+            ((t->group == 2 || t->group == 0 || t->group == BH_GROUP_LIST ||
+              t->group == BH_GROUP_SIBLINGS) && t->ppl != 1))
             return fail(BH_ERR_INVALID, "bad tuning (group 1 or 32 with ppl 1/2/4, group 4/8 with "
-                                        "ppl 1/2, group 2, 0 or BH_GROUP_LIST with ppl 1; warps "
-                                        "1..16; static_share 0..90; blocks_per_sm >= 0)");
+                                        "ppl 1/2, group 2, 0, BH_GROUP_LIST or BH_GROUP_SIBLINGS "
+                                        "with ppl 1; warps 1..16; static_share 0..90; "
+                                        "blocks_per_sm >= 0)");
         // the shape as it would be launched (BH_OPEN_INSIDE: one particle per lane)
         const WalkShape sh = shape_of(*t);
         if (walk_max_blocks_per_sm(sh, kahan(), pot()) <= 0)
@@ -821,6 +868,11 @@ struct Forest {
         TRY(clear_status());
         reset_step_counters();
         WalkShape sh{1, 8, 0, walk_group(tune.group), open_inside(), quad()};
+        if (sh.group == BH_GROUP_SIBLINGS) {  // its copy of the current tree
+            TRY(ensure_sib_bufs());
+            launch_sibling_order(bufs(), st);
+            launches += 3;
+        }
         CKR(cudaMemsetAsync(small()->wstats, 0, sizeof(small()->wstats), st));
         launch_walk(walk_args(1, d_counts.as<uint32_t>()), sh, true, false, true, nsm, st);
         launches += 1;

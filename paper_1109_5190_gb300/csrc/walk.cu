@@ -402,6 +402,142 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
     }
 }
 
+// ----------------------------------------------------- sibling-order walk
+//
+// One lane per particle, no vote, over the sibling-order copy of the records
+// (a.nodeW; every node's children are neighbours, so lanes at sibling nodes
+// share cache lines) and of the FP64 centres of mass (a.nodeD).  Each
+// particle visits the same nodes in the same order as k_walk<1, 1> (first
+// child on opening, the node after the subtree on acceptance), with the same
+// arithmetic: a cell's threshold is formed from its level exactly as the
+// topology pass forms the stored one, and a bucket reads its members through
+// its depth-first index.  So results are bit-identical.  The loop ends
+// because the build checked that the sibling order is a bijection of the
+// depth-first order, whose walk ends (skip pointers increase).
+// accept_fp64 for the sibling-order walk: the same FP64 test, with the cell's
+// level and the system's side and theta^2 in hand and the centre of mass from
+// the sibling-order copy.  (A call of its own keeps the other walks' register
+// allocation around accept_fp64 as it was.)
+__device__ __noinline__ bool accept_fp64_sib(const double4_32a *__restrict__ nodeD,
+                                             const SysStatic *__restrict__ sys,
+                                             const SysDyn *__restrict__ dyn, int sysid,
+                                             unsigned cur, int level, float px, float py,
+                                             float pz)
+{
+    const double theta2 = sys[sysid].theta2;
+    const float side = dyn[sysid].side;
+    const double4_32a D = nodeD[cur];
+    const double dx = __dsub_rn(D.y, (double)px);
+    const double dy = __dsub_rn(D.z, (double)py);
+    const double dz = __dsub_rn(D.w, (double)pz);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    const double s = (double)side * __longlong_as_double((long long)(1023 - level) << 52);
+    return __dmul_rn(s, s) < __dmul_rn(theta2, d2);
+}
+
+template <bool KAHAN, bool POT, bool COUNT>
+__global__ void __launch_bounds__(512, 3) k_walk_sib(WalkArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    Small *sm = a.small;
+    if (sm->status) return;
+    __shared__ unsigned s_next;
+    if (threadIdx.x == 0) s_next = 0;
+    __syncthreads();
+    const int per_block = (int)(((long long)a.ntiles * a.static_share / 100) / gridDim.x);
+    const int nstatic = per_block * (int)gridDim.x;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) {
+            const int k = (int)atomicAdd(&s_next, 1u);
+            t = k < per_block ? range_of_block(a.nsm) * per_block + k
+                              : nstatic + (int)atomicAdd(&sm->queue, 1u);
+        }
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= a.ntiles) break;
+        const Tile tl = a.tiles[t];
+        const SysStatic &S = a.sys[tl.sys];
+        const int sstart = S.start;
+        const float eps2 = S.eps2;
+        const float inv_theta2 = S.inv_theta2;
+        const float side = a.dyn[tl.sys].side;
+        const int myj = tl.start + lane;
+        const bool live = lane < tl.count;
+        float px = 0.f, py = 0.f, pz = 0.f;
+        unsigned cur = kLvlEnd;
+        if (live) {
+            const float4 P = a.spos[myj];
+            px = P.x; py = P.y; pz = P.z;
+            cur = (unsigned)tl.sys;  // the system's root
+        }
+        float ax = 0.f, ay = 0.f, az = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pp = 0.f, cp = 0.f;
+        unsigned cnt = 0, vis = 0, iters = 0;
+        while (cur != kLvlEnd) {
+            if (COUNT) {
+                ++iters;
+                ++vis;
+            }
+            float4 A;
+            uint4 B;
+            load_node(a.nodeW + cur, A, B);
+            const unsigned kind = (B.w >> 21) & 3u;
+            const float lscale = __int_as_float(B.w & 0x7f800000u);
+            const float lqx = (float)(short)(B.z & 0xffffu);
+            const float lqy = (float)(short)(B.z >> 16);
+            const float lqz = (float)(short)(B.w & 0xffffu);
+            const float dx = fmaf(lqx, lscale, A.x - px);
+            const float dy = fmaf(lqy, lscale, A.y - py);
+            const float dz = fmaf(lqz, lscale, A.z - pz);
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            // the threshold k_walk reads from the record: a cell's from its
+            // level (the topology pass's formula), -1 for a leaf, +inf for a
+            // bucket; the same branch structure follows, so leaves and
+            // accepted cells share one interaction path
+            const int level = (int)((B.w >> 16) & 31u);
+            const float sl = __fmul_rn(side, __int_as_float((127 - level) << 23));
+            const float ccell = __fmul_rn(__fmul_rn(sl, sl), inv_theta2);
+            const float crit = kind == kLvlCell ? ccell : (kind == kLvlLeaf ? kLeafCrit : kBucketCrit);
+            const float band = crit * kTieBand;
+            const float diff = d2 - crit;
+            bool acc = diff > 0.f;
+            if (fabsf(diff) < band)
+                acc = accept_fp64_sib(a.nodeD, a.sys, a.dyn, tl.sys, cur, level, px, py, pz);
+            if (acc) {
+                const bool self = POT && kind == kLvlLeaf && (int)B.x == myj;
+                interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az, cx, cy, cz,
+                                            pp, cp, cnt);
+                cur = B.y;
+            } else if (kind == kLvlBucket) {
+                bucket_sum<KAHAN, POT, COUNT>(a.nodeR, a.spos, (int)B.x, px, py, pz, myj, eps2,
+                                              ax, ay, az, cx, cy, cz, pp, cp, cnt);
+                cur = B.y;
+            } else {
+                cur = B.x;
+            }
+        }
+        if (COUNT) {
+            unsigned long long ci = live ? cnt : 0u, cv = live ? vis : 0u, it = iters;
+            for (int o = 16; o > 0; o >>= 1) {
+                ci += __shfl_down_sync(FULL, ci, o);
+                cv += __shfl_down_sync(FULL, cv, o);
+                it = max(it, __shfl_down_sync(FULL, it, o));
+            }
+            if (lane == 0) {
+                atomicAdd(&sm->wstats[0], ci);
+                atomicAdd(&sm->wstats[1], it);
+                atomicAdd(&sm->wstats[2], cv);
+            }
+        }
+        if (live) {
+            const uint32_t v = a.sid[myj];
+            const float G = S.G;
+            if (COUNT) a.counts[v] = cnt;
+            else S.acc[(int)v - sstart] = make_float4(G * ax, G * ay, G * az,
+                                                      POT ? -G * pp : 0.f);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- split walk
 //
 // The same per-particle decisions and the same interaction set as k_walk, in
@@ -829,6 +965,35 @@ int launch_split(const WalkArgs *a, const WalkShape &sh, int nsm, cudaStream_t s
 }
 
 template <bool KAHAN, bool POT, bool COUNT>
+int occupancy_sib(int warps)
+{
+    static int cache[33] = {0};
+    if (warps < 1 || warps > 16) return 0;
+    if (cache[warps] == 0) {
+        auto *fn = k_walk_sib<KAHAN, POT, COUNT>;
+        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, warps * 32, 0) != cudaSuccess)
+            occ = 0;
+        cache[warps] = occ > 0 ? occ : -1;
+    }
+    return cache[warps] > 0 ? cache[warps] : 0;
+}
+
+template <bool KAHAN, bool POT, bool COUNT>
+int launch_sib(const WalkArgs *a, const WalkShape &sh, int nsm, cudaStream_t st)
+{
+    if (sh.ppl != 1) return 0;
+    const int occ = occupancy_sib<KAHAN, POT, COUNT>(sh.warps);
+    if (occ <= 0) return 0;
+    if (a) {
+        const int bps = sh.blocks_per_sm > 0 ? sh.blocks_per_sm : occ;
+        k_walk_sib<KAHAN, POT, COUNT><<<nsm * bps, sh.warps * 32, 0, st>>>(*a);
+    }
+    return occ;
+}
+
+template <bool KAHAN, bool POT, bool COUNT>
 int occupancy_list(int warps)
 {
     static int cache[33] = {0};
@@ -949,6 +1114,13 @@ struct Variants {
             if (kahan) return launch_list<true, false, false>(a, sh, nsm, st);
             if (pot) return launch_list<false, true, false>(a, sh, nsm, st);
             return launch_list<false, false, false>(a, sh, nsm, st);
+        }
+        if (sh.group == BH_GROUP_SIBLINGS) {  // one lane per particle, sibling-order records
+            if (COUNT) return launch_sib<true, false, true>(a, sh, nsm, st);
+            if (kahan && pot) return launch_sib<true, true, false>(a, sh, nsm, st);
+            if (kahan) return launch_sib<true, false, false>(a, sh, nsm, st);
+            if (pot) return launch_sib<false, true, false>(a, sh, nsm, st);
+            return launch_sib<false, false, false>(a, sh, nsm, st);
         }
         if (sh.group == 0) {  // split walk
             if (COUNT) return launch_split<true, false, true>(a, sh, nsm, st);

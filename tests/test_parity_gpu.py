@@ -155,7 +155,7 @@ def test_kepler_two_body_closed_form():
         B.bh_destroy(h)
 
 
-@pytest.mark.parametrize("group", [1, 32, 0, 64])
+@pytest.mark.parametrize("group", [1, 32, 0, 64, 65])
 def test_potential_and_diagnostics(group):
     pm, vel = synth.plummer(4096, 14)
     h = make(pm, vel, eps=0.01, theta=0.5, flags=B.BH_POTENTIAL)
@@ -227,7 +227,7 @@ def test_launch_shape_does_not_change_results():
     try:
         refs, counts = {}, {}
         for group, ppl in ((1, 1), (1, 2), (1, 4), (2, 1), (4, 1), (4, 2), (8, 1), (8, 2), (32, 1),
-                           (32, 2), (32, 4), (B.BH_GROUP_LIST, 1), (0, 1)):
+                           (32, 2), (32, 4), (B.BH_GROUP_LIST, 1), (B.BH_GROUP_SIBLINGS, 1), (0, 1)):
             fam = "split" if group == 0 else "dfs"
             for w in (4, 8, 16):
                 for share in ((0, 75) if ppl == 1 else (75,)):
@@ -254,6 +254,46 @@ def test_launch_shape_does_not_change_results():
         assert np.array_equal(gpu_accel(h, n), refs["split" if best[3] == 0 else "dfs"])
     finally:
         B.bh_destroy(h)
+
+
+def test_sibling_order_walk_edge_cases():
+    # the sibling-order walk (BH_GROUP_SIBLINGS) against the depth-first walk of
+    # group 1, bit for bit: theta = 0 (every cell a bucket), one and two
+    # particles, coincident points (depth-cap buckets), a ragged tile count,
+    # and KDK steps in graph mode (the copy is rebuilt every step)
+    cases = [("theta0", synth.plummer(3000, 81), 0.0), ("one", synth.plummer(1, 82), 0.5),
+             ("two", synth.plummer(2, 83), 0.5), ("dups", gen("dups", 1000, 84), 0.7),
+             ("ragged", synth.uniform_cube(4097, 85), 0.6)]
+    for name, (pm, vel), theta in cases:
+        n = len(pm)
+        outs, counts, states = [], [], []
+        for group in (1, B.BH_GROUP_SIBLINGS):
+            h = make(pm, vel, 0.01, theta, flags=B.BH_POTENTIAL)
+            try:
+                B.bh_set_tuning(h, 1, 16, 0, group, 75)
+                outs.append(gpu_accel(h, n))
+                counts.append(B.bh_interaction_count(h, n)[0])
+                B.bh_step(h, 3, 1e-3, True)
+                x = np.zeros_like(pm); a = np.zeros_like(pm)
+                B.bh_get_state(h, x, None, a)
+                states.append((x, a))
+            finally:
+                B.bh_destroy(h)
+        assert np.array_equal(outs[0], outs[1]), name
+        assert np.array_equal(counts[0], counts[1]), name
+        assert np.array_equal(states[0][0], states[1][0]), name
+        assert np.array_equal(states[0][1], states[1][1]), name
+    # under the b_max rule the shape runs as group 1
+    pm, vel = synth.plummer(5000, 86)
+    res = []
+    for group in (1, B.BH_GROUP_SIBLINGS):
+        h = make(pm, vel, 0.01, 0.7, flags=B.BH_OPEN_BMAX)
+        try:
+            B.bh_set_tuning(h, 1, 16, 0, group, 75)
+            res.append(gpu_accel(h, 5000))
+        finally:
+            B.bh_destroy(h)
+    assert np.array_equal(res[0], res[1])
 
 
 def test_node_capacity_overflow_is_recovered():
@@ -305,10 +345,11 @@ def test_device_pointers_and_torch_stream():
         B.bh_create(B.params(), bad, d_vel)
 
 
-@pytest.mark.parametrize("group", [1, 0])
+@pytest.mark.parametrize("group", [1, 0, 65])
 def test_forest_systems_equal_alone(group):
     # group 1: one particle per lane; group 0: the split walk, whose sum order
-    # is fixed by each particle's tile, which is the same alone or in a forest
+    # is fixed by each particle's tile, which is the same alone or in a forest;
+    # 65: one particle per lane over the sibling-order records of all the trees
     systems = synth.forest_systems(12, 256, 6000, seed=19, theta=0.5, eps=0.01)
     descs = [dict(pos_mass=s.pos_mass, vel=s.vel, eps=s.eps, theta=s.theta, dt=1e-3) for s in systems]
     # give two systems other parameters: per-system theta / eps / G
@@ -564,7 +605,7 @@ def test_bmax_rule_every_shape_forest_and_options():
     try:
         ref = cref = None
         for group, ppl in ((1, 1), (1, 2), (1, 4), (2, 1), (4, 1), (8, 2), (32, 1), (32, 4),
-                           (B.BH_GROUP_LIST, 1), (0, 1)):
+                           (B.BH_GROUP_LIST, 1), (B.BH_GROUP_SIBLINGS, 1), (0, 1)):
             for w in (8, 16):
                 B.bh_set_tuning(h, ppl, w, 0, group, 75)
                 a = gpu_accel(h, n)

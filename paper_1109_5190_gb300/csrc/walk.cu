@@ -40,6 +40,8 @@
 //     writes (index < skip <= end of the system's nodes); a violation is a
 //     corrupt tree: it sets ST_WALK_LIMIT and no later kernel, the walk
 //     included, runs.
+#include <atomic>
+
 #include "bh.h"
 #include "bh_internal.cuh"
 
@@ -903,25 +905,38 @@ __global__ void __launch_bounds__(512, 3) k_walk_list(WalkArgs a)
     }
 }
 
+// A cached occupancy: computed once per (variant, block size), -1 when the
+// shape does not fit.  Host threads may race here (the server's thread and
+// the caller's); at worst both compute the same value.
+template <class F>
+int cached_occupancy(std::atomic<int> &slot, F compute)
+{
+    int c = slot.load(std::memory_order_relaxed);
+    if (c == 0) {
+        const int occ = compute();
+        c = occ > 0 ? occ : -1;
+        slot.store(c, std::memory_order_relaxed);
+    }
+    return c > 0 ? c : 0;
+}
+
 // Blocks of `warps` warps that fit on one SM, queried once per variant and
 // block size (never during stream capture: callers query before capturing).
 template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false,
           bool QUAD = false>
 int occupancy(int warps)
 {
-    static int cache[33] = {0};
+    static std::atomic<int> cache[33];
     if (warps < 1 || warps > 32) return 0;
-    if (cache[warps] == 0) {
+    return cached_occupancy(cache[warps], [warps] {
+        auto *fn = k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD>;
         // the walk uses no shared memory: give the SM's unified storage to L1
-        cudaFuncSetAttribute(k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &occ, k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD>, warps * 32, 0) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, warps * 32, 0) != cudaSuccess)
             occ = 0;
-        cache[warps] = occ > 0 ? occ : -1;
-    }
-    return cache[warps] > 0 ? cache[warps] : 0;
+        return occ;
+    });
 }
 
 // The split walk needs its queue and parked sums in shared memory: ask for
@@ -929,9 +944,9 @@ int occupancy(int warps)
 template <bool KAHAN, bool POT, bool COUNT>
 int occupancy_split(int warps)
 {
-    static int cache[33] = {0};
+    static std::atomic<int> cache[33];
     if (warps < 1 || warps > kSplitMaxWarps) return 0;
-    if (cache[warps] == 0) {
+    return cached_occupancy(cache[warps], [warps] {
         auto *fn = k_walk_split<KAHAN, POT, COUNT>;
         cudaFuncAttributes fa{};
         int occ = 0;
@@ -946,9 +961,8 @@ int occupancy_split(int warps)
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, warps * 32, 0) != cudaSuccess)
                 occ = 0;
         }
-        cache[warps] = occ > 0 ? occ : -1;
-    }
-    return cache[warps] > 0 ? cache[warps] : 0;
+        return occ;
+    });
 }
 
 template <bool KAHAN, bool POT, bool COUNT>
@@ -967,17 +981,16 @@ int launch_split(const WalkArgs *a, const WalkShape &sh, int nsm, cudaStream_t s
 template <bool KAHAN, bool POT, bool COUNT>
 int occupancy_sib(int warps)
 {
-    static int cache[33] = {0};
+    static std::atomic<int> cache[33];
     if (warps < 1 || warps > 16) return 0;
-    if (cache[warps] == 0) {
+    return cached_occupancy(cache[warps], [warps] {
         auto *fn = k_walk_sib<KAHAN, POT, COUNT>;
         cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, warps * 32, 0) != cudaSuccess)
             occ = 0;
-        cache[warps] = occ > 0 ? occ : -1;
-    }
-    return cache[warps] > 0 ? cache[warps] : 0;
+        return occ;
+    });
 }
 
 template <bool KAHAN, bool POT, bool COUNT>
@@ -996,9 +1009,9 @@ int launch_sib(const WalkArgs *a, const WalkShape &sh, int nsm, cudaStream_t st)
 template <bool KAHAN, bool POT, bool COUNT>
 int occupancy_list(int warps)
 {
-    static int cache[33] = {0};
+    static std::atomic<int> cache[33];
     if (warps < 1 || warps > kListMaxWarps) return 0;
-    if (cache[warps] == 0) {
+    return cached_occupancy(cache[warps], [warps] {
         auto *fn = k_walk_list<KAHAN, POT, COUNT>;
         cudaFuncAttributes fa{};
         int occ = 0;
@@ -1013,9 +1026,8 @@ int occupancy_list(int warps)
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, warps * 32, 0) != cudaSuccess)
                 occ = 0;
         }
-        cache[warps] = occ > 0 ? occ : -1;
-    }
-    return cache[warps] > 0 ? cache[warps] : 0;
+        return occ;
+    });
 }
 
 template <bool KAHAN, bool POT, bool COUNT>

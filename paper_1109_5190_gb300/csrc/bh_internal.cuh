@@ -121,15 +121,15 @@ struct __align__(32) WNode {
 // mass as WalkArgs::nodeD.
 // Same 32 bytes, same a, lo parts and exponent; b differs:
 //   b = (target, next, lo_xy, lo_z | level << 16 | kind << 21 | e << 23)
-//   kind kLvlCell: target = sibling-order index of the first child; the
+//   kind kSibCell: target = sibling-order index of the first child; the
 //       threshold is s^2/theta^2 from the level, as the topology pass forms it;
-//   kind kLvlLeaf: target = the particle (sorted index);
-//   kind kLvlBucket (a depth-cap bucket, or any cell when theta = 0):
+//   kind kSibLeaf: target = the particle (sorted index);
+//   kind kSibBucket (a depth-cap bucket, or any cell when theta = 0):
 //       target = the node's depth-first index (its members are in nodeR);
 //   next = sibling-order index of the node after the subtree in depth-first
-//       order, or kLvlEnd after the system's last node.
-constexpr unsigned kLvlCell = 0, kLvlLeaf = 1, kLvlBucket = 2;
-constexpr unsigned kLvlEnd = 0xffffffffu;
+//       order, or kSibEnd after the system's last node.
+constexpr unsigned kSibCell = 0, kSibLeaf = 1, kSibBucket = 2;
+constexpr unsigned kSibEnd = 0xffffffffu;
 
 #ifdef __CUDACC__
 __device__ __forceinline__ float wn_crit(const uint4 &b) { return __uint_as_float(b.x); }

@@ -739,20 +739,20 @@ k_sib_write(const SysStatic *__restrict__ sys, const uint32_t *__restrict__ noff
         const unsigned nend = noff[S.start + S.n];
         unsigned kind, target;
         if (crit == kLeafCrit) {
-            kind = kLvlLeaf;
+            kind = kSibLeaf;
             target = (unsigned)R.x;
         } else if (crit == kBucketCrit) {
-            kind = kLvlBucket;
+            kind = kSibBucket;
             target = k;
         } else {
             if (k + 1 >= nend) {  // a cell has children (true by construction)
                 atomicExch(&sm->status, ST_WALK_LIMIT);
                 return;
             }
-            kind = kLvlCell;
+            kind = kSibCell;
             target = lidx[k + 1];  // first child: the next node in depth-first order
         }
-        const unsigned next = skip < nend ? lidx[skip] : kLvlEnd;
+        const unsigned next = skip < nend ? lidx[skip] : kSibEnd;
         const unsigned meta = (W.b.w & 0xff80ffffu) | ((unsigned)R.z << 16) | (kind << 21);
         WNode F;
         F.a = W.a;

@@ -293,12 +293,12 @@ struct Forest {
         b.nodeI = quad() ? nodeI.as<double>() : nullptr;
         b.nodeQ = quad() ? nodeQ.as<float4>() : nullptr;
         b.nodeB = bmax() ? nodeB.as<double>() : nullptr;
-        const bool lvl = sib_walk() && nodeF.p;
-        b.nodeF = lvl ? nodeF.as<WNode>() : nullptr;
-        b.nodeDF = lvl ? nodeDF.as<double4_32a>() : nullptr;
-        b.lidx = lvl ? lidx.as<uint32_t>() : nullptr;
-        b.ldfs = lvl ? ldfs.as<uint32_t>() : nullptr;
-        b.sib_count = lvl ? sib_count.as<uint32_t>() : nullptr;
+        const bool sib = sib_walk() && nodeF.p;
+        b.nodeF = sib ? nodeF.as<WNode>() : nullptr;
+        b.nodeDF = sib ? nodeDF.as<double4_32a>() : nullptr;
+        b.lidx = sib ? lidx.as<uint32_t>() : nullptr;
+        b.ldfs = sib ? ldfs.as<uint32_t>() : nullptr;
+        b.sib_count = sib ? sib_count.as<uint32_t>() : nullptr;
         b.node_cap = node_cap;
         b.small = small();
         b.n_total = n_total;

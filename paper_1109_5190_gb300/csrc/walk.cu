@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(512, 3) k_walk_sib(WalkArgs a)
         const int myj = tl.start + lane;
         const bool live = lane < tl.count;
         float px = 0.f, py = 0.f, pz = 0.f;
-        unsigned cur = kLvlEnd;
+        unsigned cur = kSibEnd;
         if (live) {
             const float4 P = a.spos[myj];
             px = P.x; py = P.y; pz = P.z;
@@ -474,7 +474,7 @@ __global__ void __launch_bounds__(512, 3) k_walk_sib(WalkArgs a)
         }
         float ax = 0.f, ay = 0.f, az = 0.f, cx = 0.f, cy = 0.f, cz = 0.f, pp = 0.f, cp = 0.f;
         unsigned cnt = 0, vis = 0, iters = 0;
-        while (cur != kLvlEnd) {
+        while (cur != kSibEnd) {
             if (COUNT) {
                 ++iters;
                 ++vis;
@@ -498,18 +498,18 @@ __global__ void __launch_bounds__(512, 3) k_walk_sib(WalkArgs a)
             const int level = (int)((B.w >> 16) & 31u);
             const float sl = __fmul_rn(side, __int_as_float((127 - level) << 23));
             const float ccell = __fmul_rn(__fmul_rn(sl, sl), inv_theta2);
-            const float crit = kind == kLvlCell ? ccell : (kind == kLvlLeaf ? kLeafCrit : kBucketCrit);
+            const float crit = kind == kSibCell ? ccell : (kind == kSibLeaf ? kLeafCrit : kBucketCrit);
             const float band = crit * kTieBand;
             const float diff = d2 - crit;
             bool acc = diff > 0.f;
             if (fabsf(diff) < band)
                 acc = accept_fp64_sib(a.nodeD, a.sys, a.dyn, tl.sys, cur, level, px, py, pz);
             if (acc) {
-                const bool self = POT && kind == kLvlLeaf && (int)B.x == myj;
+                const bool self = POT && kind == kSibLeaf && (int)B.x == myj;
                 interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az, cx, cy, cz,
                                             pp, cp, cnt);
                 cur = B.y;
-            } else if (kind == kLvlBucket) {
+            } else if (kind == kSibBucket) {
                 bucket_sum<KAHAN, POT, COUNT>(a.nodeR, a.spos, (int)B.x, px, py, pz, myj, eps2,
                                               ax, ay, az, cx, cy, cz, pp, cp, cnt);
                 cur = B.y;

@@ -296,11 +296,13 @@ def test_sibling_order_walk_edge_cases():
     assert np.array_equal(res[0], res[1])
 
 
-def test_node_capacity_overflow_is_recovered():
+@pytest.mark.parametrize("group", [1, 65])
+def test_node_capacity_overflow_is_recovered(group):
     # 2048 tight pairs: every pair hangs a chain of ~17 single-child cells, so
     # the tree has ~9 nodes per particle, far above the initial capacity of
     # 2n + 1024: the build reports the overflow, the buffers grow, and the
-    # step is redone -- both for a force evaluation and inside KDK steps.
+    # step is redone -- both for a force evaluation and inside KDK steps (in
+    # graph mode too); group 65: the sibling-order copy grows with them
     rng = np.random.default_rng(17)
     c = rng.uniform(-1, 1, (2048, 3))
     pts = np.concatenate([c, c + rng.normal(0, 1e-6, c.shape)])
@@ -311,6 +313,7 @@ def test_node_capacity_overflow_is_recovered():
     vel[:, :3] = rng.normal(0, 0.1, (4096, 3))
     h = make(pm, vel, eps=0.01, theta=0.5)
     try:
+        B.bh_set_tuning(h, 1, 16, 0, group, 75)
         a = gpu_accel(h, 4096)
         T = check_tree(h, pm)
         assert T.m > 2 * 4096 + 1024
@@ -318,6 +321,9 @@ def test_node_capacity_overflow_is_recovered():
         assert_accel_close(a, ref)
         B.bh_step(h, 3, 1e-3)
         x = np.zeros_like(pm); a = np.zeros_like(pm)
+        B.bh_get_state(h, x, None, a)
+        assert_accel_close(a, oracle.Tree(x).accel(0.5, 0.01)[0])
+        B.bh_step(h, 2, 1e-3, True)
         B.bh_get_state(h, x, None, a)
         assert_accel_close(a, oracle.Tree(x).accel(0.5, 0.01)[0])
     finally:

@@ -203,6 +203,11 @@ struct Forest {
     bh_tuning g_tune{0, 0, 0, 0, 0};
     int g_ntotal = -1;
     bool g_prof = false;  // the graph carries phase events
+    bool g_sort_top = false;
+
+    // the short sort (top three digits, then runs of up to kRunMax keys put in
+    // order): on until a build meets a longer run, then the full sort for good
+    bool sort_top = true;
 
     // first level of the fused deep centre-of-mass launch, chosen from the
     // previous build's level sizes (22 = none yet)
@@ -304,6 +309,7 @@ struct Forest {
         b.n_total = n_total;
         b.nsm = nsm;
         b.deep_cut = deep_cut;
+        b.sort_top = sort_top ? 1 : 0;
         return b;
     }
 
@@ -642,6 +648,7 @@ struct Forest {
         g_nsteps = nsteps;
         g_cap = node_cap;
         g_tune = tune;
+        g_sort_top = sort_top;
         g_ntotal = n_total;
         return BH_OK;
     }
@@ -659,7 +666,8 @@ struct Forest {
             if (graph) {
                 walk_max_blocks_per_sm(shape(), kahan(), pot());  // occupancy query outside capture
                 if (!gexec || g_nsteps != remaining || g_cap != node_cap || g_ntotal != n_total ||
-                    std::memcmp(&g_tune, &tune, sizeof tune) != 0 || (prof && !g_prof))
+                    g_sort_top != sort_top || std::memcmp(&g_tune, &tune, sizeof tune) != 0 ||
+                    (prof && !g_prof))
                     TRY(capture_graph(remaining));
                 CKR(cudaGraphLaunch(gexec, st));
                 launches += (int64_t)remaining * steps_launches();
@@ -681,6 +689,15 @@ struct Forest {
             if (h.status == ST_OK) {
                 remaining = 0;
                 break;
+            }
+            if (h.status == ST_SORT_LONG) {  // redo with the full sort, from here on
+                const int done = (int)h.steps_done;
+                launch_restore(bufs(), st);
+                launches += 1;
+                sort_top = false;
+                remaining -= done;
+                tree_valid = false;
+                continue;
             }
             if (h.status == ST_CAPACITY) {
                 const int done = (int)h.steps_done;

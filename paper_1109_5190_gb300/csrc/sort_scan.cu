@@ -3,8 +3,9 @@
 //
 // The sort orders each system's particles by key; it is stable, and keys
 // are produced in input order, so equal keys (coincident points at the depth
-// cap) end up ordered by input index.  Eight passes of 8 bits each; every
-// pass is histogram -> exclusive scan -> stable scatter.  Segmentation costs
+// cap) end up ordered by input index.  Eight passes of 8 bits each (or the top
+// three, then a fixup of short runs: see k_rs_fixup); every pass is
+// histogram -> exclusive scan -> stable scatter.  Segmentation costs
 // nothing extra: the per-(chunk, digit) counts are laid out system by system
 // as [system][digit][chunk], so one global exclusive scan yields offsets that
 // already include every earlier system's particles (chunks never straddle
@@ -358,6 +359,71 @@ void prepare_sort_kernels()
                          (int)kScatterSmem);
 }
 
+// The short sort: LSD passes over the top three digits (key bits 40..63) only,
+// so the keys end up ordered by their top 24 bits, ties in input order.  A run
+// of keys equal there (particles sharing a cell of about level 8) is then put
+// in order by its full key, stably, which gives exactly the (key, input
+// index) order of the full sort.  The fixup also moves the result from the
+// second buffer (three passes) back to the first.
+constexpr int kTopFirstPass = 5;
+constexpr int kTopShift = kTopFirstPass * kRadixBits;
+constexpr int kRunMax = 8;
+
+__global__ void __launch_bounds__(kWideThreads)
+k_rs_fixup(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+           uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
+           const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+           Small *__restrict__ sm)
+{
+    if (sm->status) return;
+    const int4 c = chunks[blockIdx.x];
+    const SysStatic S = sys[c.x];
+    const int send = S.start + S.n;
+    for (int k = 0; k < kWideItems; ++k) {
+        const int i = k * kWideThreads + threadIdx.x;
+        if (i >= c.z) break;
+        const int j = c.y + i;
+        const uint64_t kj = kin[j];
+        const uint64_t pj = kj >> kTopShift;
+        // a run is written by the thread of its first key
+        if (j > S.start && (kin[j - 1] >> kTopShift) == pj) continue;
+        int len = 1;
+        while (len <= kRunMax && j + len < send && (kin[j + len] >> kTopShift) == pj) ++len;
+        if (len > kRunMax) {
+            atomicExch(&sm->status, ST_SORT_LONG);
+            continue;
+        }
+        if (len == 1) {
+            kout[j] = kj;
+            vout[j] = vin[j];
+            continue;
+        }
+        uint64_t rk[kRunMax];
+        uint32_t rv[kRunMax];
+        for (int q = 0; q < len; ++q) {
+            rk[q] = kin[j + q];
+            rv[q] = vin[j + q];
+        }
+        // insertion sort, stable: an element moves only past larger keys
+        for (int q = 1; q < len; ++q) {
+            const uint64_t x = rk[q];
+            const uint32_t y = rv[q];
+            int p = q;
+            while (p > 0 && rk[p - 1] > x) {
+                rk[p] = rk[p - 1];
+                rv[p] = rv[p - 1];
+                --p;
+            }
+            rk[p] = x;
+            rv[p] = y;
+        }
+        for (int q = 0; q < len; ++q) {
+            kout[j + q] = rk[q];
+            vout[j + q] = rv[q];
+        }
+    }
+}
+
 void launch_sort(const BuildBufs &b, cudaStream_t st)
 {
     uint64_t *kin = b.key0, *kout = b.key1;
@@ -366,9 +432,11 @@ void launch_sort(const BuildBufs &b, cudaStream_t st)
     // two count buffers: pass p scans and reads one while its scatter counts
     // the next pass's digits into the other (zeroed just before)
     uint32_t *cur = b.rs_counts, *nxt = b.rs_counts + ncounts;
-    k_rs_hist<<<b.nchunks, kSortThreads, 0, st>>>(kin, b.chunks, b.sys, cur, 0, b.small);
+    const int first = b.sort_top ? kTopFirstPass : 0;
+    k_rs_hist<<<b.nchunks, kSortThreads, 0, st>>>(kin, b.chunks, b.sys, cur, first * kRadixBits,
+                                                  b.small);
     g_launches += 1;
-    for (int pass = 0; pass < kRadixPasses; ++pass) {
+    for (int pass = first; pass < kRadixPasses; ++pass) {
         const int shift = pass * kRadixBits;
         const bool more = pass + 1 < kRadixPasses;
         // the scan also clears the count buffer this pass's scatter fills
@@ -380,6 +448,11 @@ void launch_sort(const BuildBufs &b, cudaStream_t st)
         uint64_t *tk = kin; kin = kout; kout = tk;
         uint32_t *tv = vin; vin = vout; vout = tv;
         uint32_t *tc = cur; cur = nxt; nxt = tc;
+    }
+    if (b.sort_top) {  // three passes: the keys are in the second buffers
+        k_rs_fixup<<<b.nchunks, kWideThreads, 0, st>>>(kin, vin, b.key0, b.val0, b.chunks, b.sys,
+                                                       b.small);
+        g_launches += 1;
     }
 }
 

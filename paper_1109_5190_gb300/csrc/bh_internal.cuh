@@ -47,7 +47,7 @@ constexpr float kTieBand = 4e-6f;
 
 // device status codes (0 = ok)
 // ST_SORT_LONG: the short sort met a run of more than kRunMax keys equal in
-// their top 24 bits; the step is redone with the full sort
+// their sorted top digits; the step is redone with one digit more
 enum : int { ST_OK = 0, ST_CAPACITY = 1, ST_WALK_LIMIT = 2, ST_BAD_INPUT = 3, ST_SORT_LONG = 4 };
 
 // per-system modes of one step
@@ -183,10 +183,10 @@ struct BuildBufs {
     uint64_t *key0, *key1;
     uint32_t *val0, *val1;
     uint32_t *rs_counts;  // kRadixBins * nchunks
-    // 1: sort by the top three digits only, then put each run of keys equal
-    // there in order (ST_SORT_LONG if a run is longer than kRunMax); 0: all
-    // eight digits
-    int sort_top;
+    // first radix pass: 0 = all eight digits; k > 0 = passes k..7 only (the
+    // top 8 - k digits), then each run of keys equal there is put in order
+    // (ST_SORT_LONG if a run is longer than kRunMax)
+    int sort_first;
     uint32_t *scan_part;  // scan partials
     float4 *spos;
     uint32_t *ncount;     // n_total + 1

@@ -203,11 +203,12 @@ struct Forest {
     bh_tuning g_tune{0, 0, 0, 0, 0};
     int g_ntotal = -1;
     bool g_prof = false;  // the graph carries phase events
-    bool g_sort_top = false;
+    int g_sort_first = -1;
 
-    // the short sort (top three digits, then runs of up to kRunMax keys put in
-    // order): on until a build meets a longer run, then the full sort for good
-    bool sort_top = true;
+    // the short sort's first radix pass: the top three digits to start with;
+    // a build that meets a longer run than the fixup sorts is redone with one
+    // digit more, down to the full sort (0), which then stays
+    int sort_first = 5;
 
     // first level of the fused deep centre-of-mass launch, chosen from the
     // previous build's level sizes (22 = none yet)
@@ -309,7 +310,7 @@ struct Forest {
         b.n_total = n_total;
         b.nsm = nsm;
         b.deep_cut = deep_cut;
-        b.sort_top = sort_top ? 1 : 0;
+        b.sort_first = sort_first;
         return b;
     }
 
@@ -648,7 +649,7 @@ struct Forest {
         g_nsteps = nsteps;
         g_cap = node_cap;
         g_tune = tune;
-        g_sort_top = sort_top;
+        g_sort_first = sort_first;
         g_ntotal = n_total;
         return BH_OK;
     }
@@ -659,14 +660,15 @@ struct Forest {
     {
         int remaining = nsteps;
         for (int attempt = 0; remaining > 0; ++attempt) {
-            if (attempt > 8) return fail(BH_ERR_CAPACITY, "node buffer kept overflowing");
+            // each retry grows the node buffer or adds a sort digit (at most 5)
+            if (attempt > 16) return fail(BH_ERR_CAPACITY, "node buffer kept overflowing");
             TRY(clear_status());
             TRY(ensure_tiles(tune.ppl));
             TRY(ensure_sib_bufs());
             if (graph) {
                 walk_max_blocks_per_sm(shape(), kahan(), pot());  // occupancy query outside capture
                 if (!gexec || g_nsteps != remaining || g_cap != node_cap || g_ntotal != n_total ||
-                    g_sort_top != sort_top || std::memcmp(&g_tune, &tune, sizeof tune) != 0 ||
+                    g_sort_first != sort_first || std::memcmp(&g_tune, &tune, sizeof tune) != 0 ||
                     (prof && !g_prof))
                     TRY(capture_graph(remaining));
                 CKR(cudaGraphLaunch(gexec, st));
@@ -690,11 +692,11 @@ struct Forest {
                 remaining = 0;
                 break;
             }
-            if (h.status == ST_SORT_LONG) {  // redo with the full sort, from here on
+            if (h.status == ST_SORT_LONG) {  // redo with one more digit, from here on
                 const int done = (int)h.steps_done;
                 launch_restore(bufs(), st);
                 launches += 1;
-                sort_top = false;
+                sort_first = sort_first > 0 ? sort_first - 1 : 0;
                 remaining -= done;
                 tree_valid = false;
                 continue;

@@ -3,8 +3,8 @@
 //
 // The sort orders each system's particles by key; it is stable, and keys
 // are produced in input order, so equal keys (coincident points at the depth
-// cap) end up ordered by input index.  Eight passes of 8 bits each (or the top
-// three, then a fixup of short runs: see k_rs_fixup); every pass is
+// cap) end up ordered by input index.  Eight passes of 8 bits each (or only the
+// top few, then a fixup of short runs: see k_rs_fixup); every pass is
 // histogram -> exclusive scan -> stable scatter.  Segmentation costs
 // nothing extra: the per-(chunk, digit) counts are laid out system by system
 // as [system][digit][chunk], so one global exclusive scan yields offsets that
@@ -359,20 +359,19 @@ void prepare_sort_kernels()
                          (int)kScatterSmem);
 }
 
-// The short sort: LSD passes over the top three digits (key bits 40..63) only,
-// so the keys end up ordered by their top 24 bits, ties in input order.  A run
-// of keys equal there (particles sharing a cell of about level 8) is then put
-// in order by its full key, stably, which gives exactly the (key, input
-// index) order of the full sort.  The fixup also moves the result from the
-// second buffer (three passes) back to the first.
-constexpr int kTopFirstPass = 5;
-constexpr int kTopShift = kTopFirstPass * kRadixBits;
+// The short sort: LSD passes over the top digits only (passes first..7, key
+// bits 8 * first..63), so the keys end up ordered by those bits, ties in input
+// order.  A run of keys equal there (particles sharing a cell of about level
+// (63 - 8 * first) / 3) is then put in order by its full key, stably, which
+// gives exactly the (key, input index) order of the full sort.  The fixup
+// writes the result to the first buffers (from the second after an odd
+// number of passes).
 constexpr int kRunMax = 8;
 
 __global__ void __launch_bounds__(kWideThreads)
 k_rs_fixup(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
            uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
-           const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
+           const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys, int kTopShift,
            Small *__restrict__ sm)
 {
     if (sm->status) return;
@@ -432,7 +431,7 @@ void launch_sort(const BuildBufs &b, cudaStream_t st)
     // two count buffers: pass p scans and reads one while its scatter counts
     // the next pass's digits into the other (zeroed just before)
     uint32_t *cur = b.rs_counts, *nxt = b.rs_counts + ncounts;
-    const int first = b.sort_top ? kTopFirstPass : 0;
+    const int first = b.sort_first;
     k_rs_hist<<<b.nchunks, kSortThreads, 0, st>>>(kin, b.chunks, b.sys, cur, first * kRadixBits,
                                                   b.small);
     g_launches += 1;
@@ -449,9 +448,9 @@ void launch_sort(const BuildBufs &b, cudaStream_t st)
         uint32_t *tv = vin; vin = vout; vout = tv;
         uint32_t *tc = cur; cur = nxt; nxt = tc;
     }
-    if (b.sort_top) {  // three passes: the keys are in the second buffers
+    if (first > 0) {  // the keys are in kin: the second buffers after an odd pass count
         k_rs_fixup<<<b.nchunks, kWideThreads, 0, st>>>(kin, vin, b.key0, b.val0, b.chunks, b.sys,
-                                                       b.small);
+                                                       first * kRadixBits, b.small);
         g_launches += 1;
     }
 }

@@ -7,8 +7,8 @@
  *
  * What it computes follows the paper (Dekate et al., arXiv:1109.5190):
  *   - Section I: the N-body problem -- n particles evolving under pairwise
- *     gravity -- and the Barnes-Hut octree "subdivided until there is one
- *     particle per sub-cube", with a centre of mass per cube.
+ *     gravity -- and the Barnes-Hut octree, whose cubes are split into eight
+ *     until each leaf holds a single particle, with a centre of mass per cube.
  *   - Section III (Fig. 1): a remote cluster is replaced by one body when the
  *     distance D to it exceeds r/theta; smaller theta means smaller error.
  *   - Section III (Fig. 2): a worked 2-D example where a cluster of two

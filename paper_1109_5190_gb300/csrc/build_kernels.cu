@@ -3,10 +3,11 @@
 // keys, the gather into Morton order, the octree topology, the bottom-up
 // centre-of-mass pass, the closing kick, diagnostics and the tree export.
 //
-// Paper: Dekate et al., arXiv:1109.5190.  Section I: particles grouped by a
-// hierarchy of cubes subdivided until there is one particle per sub-cube,
-// with a centre of mass per cube; Section III: the tree is rebuilt from all
-// positions in every iteration (a global barrier), then forces are computed.
+// Paper: Dekate et al., arXiv:1109.5190.  Section I: the particles are grouped
+// in nested cubes, each split into eight until every leaf holds a single
+// particle, with a centre of mass per cube; Section III: the tree is rebuilt
+// from all positions in every iteration (a global barrier), then forces are
+// computed.
 // Every kernel here is HBM-bound streaming work (no tensor cores): loads are
 // coalesced float4, one block per chunk of <= 4096 particles of one system.
 #include "bh.h"

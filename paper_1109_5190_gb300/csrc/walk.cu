@@ -1,5 +1,5 @@
-// walk.cu -- the Barnes-Hut force walk (the "force computation stage" of
-// Section III, the most computationally intensive part of the method).
+// walk.cu -- the Barnes-Hut force walk: the per-particle force phase, which
+// Section III names as the costliest phase of the method.
 //
 // For each particle i the walk sums, over the cells it accepts and the leaf
 // particles it reaches, G m_j (x_j - x_i) / (|x_j - x_i|^2 + eps^2)^(3/2).  A

@@ -690,6 +690,44 @@ def test_checkpoint_resume_is_bit_exact():
             assert np.array_equal(g, w), route
 
 
+def test_short_sort_escalates_inside_graph_steps():
+    # the sort orders by its top digits and fixes up short runs; a longer run
+    # makes the step roll back and rerun with one more digit.  Steps that meet
+    # that in the middle of a captured multi-step graph (a clustered state set
+    # into a system that ran uniform steps with the three-digit sort) give
+    # bit for bit what a fresh system gives: the order is the full sort's
+    # whatever the number of digits
+    n = 20000
+    pm_u, vel_u = synth.uniform_cube(n, 91)
+    pm_c, vel_c = synth.plummer(n, 92)  # dense core: runs far longer than the fixup sorts
+    h = make(pm_c, vel_c, 0.01, 0.6)
+    try:
+        acc_c = gpu_accel(h, n)
+    finally:
+        B.bh_destroy(h)
+    h = make(pm_u, vel_u, 0.01, 0.6)
+    try:
+        B.bh_step(h, 4, 1e-3, True)
+        # with the acceleration given, the next steps start in the graph, whose
+        # first rebuild meets the long runs
+        B.bh_set_state(h, pm_c, vel_c, acc_c)
+        B.bh_step(h, 5, 1e-3, True)
+        got = [np.zeros_like(pm_c) for _ in range(3)]
+        B.bh_get_state(h, *got)
+    finally:
+        B.bh_destroy(h)
+    h = make(pm_c, vel_c, 0.01, 0.6)
+    try:
+        B.bh_step(h, 5, 1e-3, True)
+        want = [np.zeros_like(pm_c) for _ in range(3)]
+        B.bh_get_state(h, *want)
+        T = check_tree(h, want[0])  # keys, order and topology against the oracle
+    finally:
+        B.bh_destroy(h)
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w)
+
+
 def test_bmax_rule_theta_zero_and_served():
     # theta = 0 never accepts under either rule: the walk is the direct sum,
     # bit-identical with and without the rule; and a server created with the

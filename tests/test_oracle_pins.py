@@ -534,3 +534,34 @@ def test_bmax_rule_never_accepts_the_particles_own_cell(oracle_lib):
         _, _, d1 = T.accel(theta, 0.01, open_inside=True)
         assert np.any(d0 != d1)
 
+
+
+# ---------------------------------------------------- many-body invariants
+
+def _energy(pm, v, eps):
+    _, phi = oracle.direct(pm, eps)
+    m = pm[:, 3]
+    return 0.5 * (m * (v ** 2).sum(1)).sum() + 0.5 * (m * phi).sum()
+
+
+def test_leapfrog_many_body_conservation_laws(oracle_lib):
+    # theta = 0 (every pair summed directly, softened central forces): total
+    # momentum and angular momentum are conserved to rounding by every KDK
+    # step, and the energy error of the symplectic scheme is second order in
+    # dt -- halving dt quarters it -- for a Plummer sphere of 256 bodies
+    pm, vel = synth.plummer(256, 31)
+    pm = pm.astype(np.float64); v0 = vel[:, :3].astype(np.float64)
+    eps = 0.05
+    e0 = _energy(pm, v0, eps)
+    m = pm[:, 3]
+    p0 = (m[:, None] * v0).sum(0)
+    l0 = (m[:, None] * np.cross(pm[:, :3], v0)).sum(0)
+    errs = []
+    for nsteps, dt in ((20, 2e-2), (40, 1e-2), (80, 5e-3)):
+        p, v, _ = oracle.leapfrog(pm, vel, nsteps, dt, theta=0.0, eps=eps)
+        mv = m[:, None] * v
+        assert np.abs(mv.sum(0) - p0).max() < 1e-14
+        assert np.abs((m[:, None] * np.cross(p[:, :3], v)).sum(0) - l0).max() < 1e-13
+        errs.append(abs(_energy(p, v, eps) - e0) / abs(e0))
+    assert errs[0] < 1e-3
+    assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0, errs

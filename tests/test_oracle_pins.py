@@ -565,3 +565,22 @@ def test_leapfrog_many_body_conservation_laws(oracle_lib):
         errs.append(abs(_energy(p, v, eps) - e0) / abs(e0))
     assert errs[0] < 1e-3
     assert 3.0 < errs[0] / errs[1] < 5.0 and 3.0 < errs[1] / errs[2] < 5.0, errs
+
+
+def test_walk_linear_in_masses_and_G_and_independent_of_input_order(oracle_lib):
+    # the tree depends on positions only, so scaling every mass by 2 and G by
+    # 4 scales every acceleration and potential by exactly 8 (powers of two);
+    # and the canonical tree and depth-first sum order make every particle's
+    # result independent of the order the particles are given in
+    pm, _ = synth.plummer(1500, 33)
+    pm = pm.astype(np.float64)
+    pm[:, 3] *= np.linspace(0.5, 1.5, len(pm))
+    for theta in (0.0, 0.6, 1.0):
+        a, p, c = oracle.Tree(pm).accel(theta, 0.01)
+        q = pm.copy(); q[:, 3] *= 2.0
+        a2, p2, c2 = oracle.Tree(q).accel(theta, 0.01, G=4.0)
+        assert np.array_equal(c2, c) and np.array_equal(a2, 8.0 * a) and np.array_equal(p2, 8.0 * p)
+        perm = np.random.default_rng(34).permutation(len(pm))
+        a3, p3, c3 = oracle.Tree(pm[perm]).accel(theta, 0.01)
+        assert np.array_equal(c3, c[perm]) and np.array_equal(a3, a[perm])
+        assert np.array_equal(p3, p[perm])

@@ -728,6 +728,34 @@ def test_short_sort_escalates_inside_graph_steps():
         assert np.array_equal(g, w)
 
 
+def test_linear_in_masses_and_G_and_independent_of_input_order():
+    # as for the oracle: ×2 masses and ×4 G scale every acceleration and
+    # potential by exactly 8 (the tree depends on positions only; FP64 centres
+    # of mass, FP32 terms and Kahan sums scale exactly by powers of two), and a
+    # permutation of the input gives every particle its result bit for bit
+    # (distinct keys: the sorted order and every walk are the same)
+    n = 12000
+    pm, vel = synth.plummer(n, 93)
+    pm = pm.copy()
+    pm[:, 3] *= np.linspace(0.5, 1.5, n).astype(np.float32)
+    outs = {}
+    for tag, q, G in (("base", pm, 1.0), ("scaled", pm * np.float32([1, 1, 1, 2]), 4.0)):
+        h = B.bh_create(B.params(G, 0.01, 0.6, B.BH_POTENTIAL), q, vel)
+        try:
+            outs[tag] = gpu_accel(h, n)
+        finally:
+            B.bh_destroy(h)
+    assert np.array_equal(outs["scaled"], 8.0 * outs["base"])
+    perm = np.random.default_rng(94).permutation(n)
+    h = make(pm[perm], vel[perm], 0.01, 0.6, flags=B.BH_POTENTIAL)
+    try:
+        a = gpu_accel(h, n)
+    finally:
+        B.bh_destroy(h)
+    assert len(np.unique(oracle.keys(pm))) == n  # distinct keys
+    assert np.array_equal(a, outs["base"][perm])
+
+
 def test_bmax_rule_theta_zero_and_served():
     # theta = 0 never accepts under either rule: the walk is the direct sum,
     # bit-identical with and without the rule; and a server created with the

@@ -202,6 +202,35 @@ def cpu_sample(pm, sample: int, seed: int = 7):
     return n / t_step, t2 - t0, threads
 
 
+def cpu_one_core(pm, sample: int = 4096, seed: int = 8):
+    """The same oracle step with the walk on one thread (a smaller sample):
+    (particle-steps/s, seconds spent)."""
+    import numpy as np
+    import oracle
+    n = len(pm)
+    t0 = time.perf_counter()
+    T = oracle.Tree(pm)
+    t1 = time.perf_counter()
+    idx = np.random.default_rng(seed).choice(n, min(sample, n), replace=False)
+    T.accel(THETA, EPS, targets=idx, nthreads=1)
+    t2 = time.perf_counter()
+    return n / ((t1 - t0) + (t2 - t1) * n / len(idx)), t2 - t0
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -360,10 +389,15 @@ def run_gpu(args):
     line.update(extra)
     if rank == 0 and ws == 1 and not args.no_cpu:
         v, spent, threads = cpu_sample(pm, args.cpu_sample)
+        v1, spent1 = cpu_one_core(pm)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"one step: full FP64 tree build of {N_PART} particles "
                                           f"(1 thread) + walk of {args.cpu_sample} random particles "
-                                          f"({threads} threads), extrapolated to N; {spent:.1f} s"}
+                                          f"({threads} threads), extrapolated to N; {spent:.1f} s",
+                                "one_core_value": v1,
+                                "one_core_sample": f"the same step with a 4096-particle walk on "
+                                                   f"1 thread, extrapolated to N; {spent1:.1f} s",
+                                "cpu_model": cpu_model()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -138,7 +138,9 @@ typedef struct bh_node {
  *                   tree in which every node's children sit next to each
  *                   other, so lanes at sibling nodes share cache lines.  Not
  *                   available with BH_OPEN_INSIDE, BH_QUADRUPOLE or
- *                   BH_OPEN_BMAX (it runs as group 1 there).
+ *                   BH_OPEN_BMAX (it runs as group 1 there).  Measured
+ *                   slower than group 1 on the workloads tried, so
+ *                   bh_autotune does not consider it (nor BH_GROUP_LIST).
  * Accelerations are bit-identical for every shape with group >= 1 (the
  * interaction lists and the sibling-order walk included).  The split
  * walk sums the same terms in another order, fixed by each particle's tile (32

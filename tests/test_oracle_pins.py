@@ -584,3 +584,44 @@ def test_walk_linear_in_masses_and_G_and_independent_of_input_order(oracle_lib):
         a3, p3, c3 = oracle.Tree(pm[perm]).accel(theta, 0.01)
         assert np.array_equal(c3, c[perm]) and np.array_equal(a3, a[perm])
         assert np.array_equal(p3, p[perm])
+
+
+# ---------------------------------------------------------- input recipes
+
+def test_input_recipes_match_their_statements():
+    # the seeded generators hold no method arithmetic; these check the input
+    # recipes as stated: determinism per seed, the uniform cube's range and
+    # masses, the forest's size law and kinds, and the request stream's rate
+    # and ranges
+    a1, v1 = synth.uniform_cube(4096, 3)
+    a2, v2 = synth.uniform_cube(4096, 3)
+    b1, _ = synth.uniform_cube(4096, 4)
+    assert np.array_equal(a1, a2) and np.array_equal(v1, v2) and not np.array_equal(a1, b1)
+    assert a1.dtype == np.float32 and np.abs(a1[:, :3]).max() <= 1.0
+    assert np.all(a1[:, 3] == np.float32(1.0 / 4096)) and not np.any(v1[:, :3])
+    p1, _ = synth.plummer(2048, 5)
+    p2, _ = synth.plummer(2048, 5)
+    assert np.array_equal(p1, p2)
+    # forest: N log-uniform in [256, 65536]; even index Plummer, odd uniform
+    fs = synth.forest_systems(512, 256, 65536, seed=4, materialise=False)
+    ns = np.array([s.n for s in fs])
+    assert ns.min() >= 256 and ns.max() <= 65536
+    logs = np.log(ns)
+    # a log-uniform law has its median at the geometric mean and the
+    # variance of U(log 256, log 65536)
+    assert abs(np.median(logs) - 0.5 * (np.log(256) + np.log(65536))) < 0.35
+    assert abs(logs.var() - (np.log(65536 / 256)) ** 2 / 12) < 0.5
+    assert all(s.kind == ("plummer" if k % 2 == 0 else "uniform") for k, s in enumerate(fs))
+    # request stream: Poisson arrivals at 200/s for 60 s, N log-uniform in
+    # [1024, 2097152], theta in [0.5, 0.8], 10..200 steps
+    rs = synth.request_stream(200.0, 60.0, seed=5)
+    t = np.array([r.arrival_s for r in rs])
+    assert abs(len(rs) - 12000) < 4 * np.sqrt(12000)
+    gaps = np.diff(np.concatenate([[0.0], t]))
+    assert abs(gaps.mean() - 1 / 200) < 0.05 / 200 and abs(gaps.std() / gaps.mean() - 1) < 0.05
+    n = np.array([r.n for r in rs])
+    th = np.array([r.theta for r in rs])
+    st = np.array([r.steps for r in rs])
+    assert n.min() >= 1024 and n.max() <= 2097152
+    assert th.min() >= 0.5 and th.max() <= 0.8 and st.min() >= 10 and st.max() <= 200
+    assert abs(np.mean([r.kind == "plummer" for r in rs]) - 0.5) < 0.02

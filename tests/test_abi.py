@@ -89,6 +89,18 @@ def test_host_side_argument_errors(lib):
     p = B.params(flags=0x40)  # no such flag
     assert B.lib.bh_create(ctypes.byref(h), ctypes.byref(p), 4, pm.ctypes.data, None, None, 0) \
         == B.BH_ERR_INVALID
+    # quadrupoles need Kahan sums: rejected before any device work, for a
+    # system, a forest and a server alike
+    p = B.params(flags=B.BH_QUADRUPOLE | B.BH_NO_KAHAN)
+    assert B.lib.bh_create(ctypes.byref(h), ctypes.byref(p), 4, pm.ctypes.data, None, None, 0) \
+        == B.BH_ERR_INVALID
+    assert "Kahan" in B.last_error()
+    d = (B.bh_system_desc * 1)()
+    d[0].n, d[0].pos_mass, d[0].G, d[0].eps, d[0].theta, d[0].dt = 4, pm.ctypes.data, 1.0, 0.01, 0.5, 1e-3
+    for fl in (B.BH_QUADRUPOLE | B.BH_NO_KAHAN, 0x40):
+        assert B.lib.bh_forest_create(ctypes.byref(h), 1, d, None, fl) == B.BH_ERR_INVALID
+        assert B.lib.bh_server_create(ctypes.byref(h), 1 << 30, 2, None, fl) == B.BH_ERR_INVALID
+    assert B.lib.bh_server_create(ctypes.byref(h), 1 << 10, 2, None, 0) == B.BH_ERR_INVALID  # budget
     assert B.lib.bh_step(None, 1, 1e-3, 0) == B.BH_ERR_INVALID
     assert B.lib.bh_poll(None, 1, None) == B.BH_ERR_INVALID
     assert B.lib.bh_version().decode().startswith("bh-gb300")

@@ -369,17 +369,28 @@ int bh_server_destroy(bh_server *s);
  * Computes, for n particles (pos_mass: device, n x 4 floats), the same 63-bit
  * Morton keys as the tree build (keys: device, n uint64, input order) and the
  * key cube (cube: device, 4 floats lo_x, lo_y, lo_z, side; may be NULL).
+ * Masses are not read.  Each pointer must be memory of the current device (or
+ * managed memory), pos_mass 16-byte, keys 8-byte and cube 4-byte aligned;
+ * anything else (a host pointer, another device's memory, an offset that
+ * breaks the alignment) returns BH_ERR_INVALID before any work is enqueued.
  * Allocates nothing and calls no allocating routine: its only scratch is a
  * file-scope device array of 128 KiB + 32 bytes (per-chunk boxes), held on
  * every GPU that loads the library until the process exits.  n must be in
  * [1, BH_NOALLOC_MAX_N]; larger n returns BH_ERR_INVALID with a message.
  * The work is enqueued on `stream` (NULL = legacy default stream) and the call
- * returns without synchronising.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  Every call on a device
- * shares its array and overwrites what it reads, so calls whose work
+ * returns without synchronising, so input the tree build would reject cannot
+ * come back as a status: if any coordinate is non-finite, every key is set to
+ * BH_NOALLOC_BAD_KEY (no 63-bit key has that value) and the cube to NaN.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the rest
+ * of the process; make that first call before any stream capture.  A
+ * cudaDeviceReset ends the context holding the array, so the kept address is
+ * stale afterwards: do not call this entry point again in that process (the
+ * library's other handles do not survive a reset either).  Every call on a
+ * device shares its array and overwrites what it reads, so calls whose work
  * overlaps on one GPU race: keep them on one stream or order them. */
 #define BH_NOALLOC_MAX_N 16777216
+#define BH_NOALLOC_BAD_KEY 0xffffffffffffffffull
 int bh_morton_keys_noalloc(const float *pos_mass, int64_t n, uint64_t *keys, float *cube,
                            void *stream);
 

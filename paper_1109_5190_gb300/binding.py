@@ -448,20 +448,35 @@ def bh_server_destroy(h):
 # ------------------------------------------------- allocation-free Morton keys
 
 BH_NOALLOC_MAX_N = 16777216
+BH_NOALLOC_BAD_KEY = 0xffffffffffffffff
 
 
 def bh_morton_keys_noalloc(pos_mass, keys, cube=None, stream=None):
     """Keys of device pos_mass (n x 4 float32) into device keys (n int64 /
     uint64 tensor) and cube (4 float32 or None); enqueued on `stream`, no
-    allocation.  For callers that cannot allocate device memory."""
-    n = pos_mass.numel() // 4
-    if not (_is_torch(pos_mass) and pos_mass.is_cuda and _is_torch(keys) and keys.is_cuda):
-        raise ValueError("device tensors required")
-    if keys.numel() != n or keys.element_size() != 8:
-        raise ValueError("keys must hold n 64-bit values")
+    allocation.  For callers that cannot allocate device memory.  Every
+    tensor must be a contiguous CUDA tensor of the stated type and size."""
+    import torch
+    for name, t in (("pos_mass", pos_mass), ("keys", keys), ("cube", cube)):
+        if t is None and name == "cube":
+            continue
+        if not (_is_torch(t) and t.is_cuda and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if pos_mass.dtype != torch.float32 or pos_mass.dim() != 2 or pos_mass.shape[1] != 4:
+        raise ValueError("pos_mass must be float32 of shape (n, 4)")
+    n = pos_mass.shape[0]
+    if keys.dtype not in (torch.int64, getattr(torch, "uint64", torch.int64)) or keys.numel() != n:
+        raise ValueError("keys must hold n 64-bit integers")
+    if cube is not None and (cube.dtype != torch.float32 or cube.numel() < 4):
+        raise ValueError("cube must be float32 with at least 4 values")
+    devs = {t.device for t in (pos_mass, keys, cube) if t is not None}
+    if len(devs) != 1:
+        raise ValueError("pos_mass, keys and cube must be on one device")
     cp = C.c_void_p(cube.data_ptr()) if cube is not None else None
-    return _check(lib.bh_morton_keys_noalloc(C.c_void_p(pos_mass.data_ptr()), n,
-                                             C.c_void_p(keys.data_ptr()), cp, _stream(stream)))
+    with torch.cuda.device(pos_mass.device):
+        return _check(lib.bh_morton_keys_noalloc(C.c_void_p(pos_mass.data_ptr()), n,
+                                                 C.c_void_p(keys.data_ptr()), cp,
+                                                 _stream(stream)))
 
 
 # ---------------------------------------------------------- micro-benchmarks

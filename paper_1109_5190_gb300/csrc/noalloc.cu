@@ -19,6 +19,13 @@
 // Keys follow the same rule as the main path: cube anchored at the per-axis
 // minimum, side = largest FP32 extent (1 if below 1e-30), 21-bit FP32
 // round-to-nearest quantisation, x bit most significant in each triple.
+//
+// The main path rejects non-finite coordinates before it builds a tree; this
+// call returns before its kernels run, so it marks such input in its outputs
+// instead: every key becomes BH_NOALLOC_BAD_KEY (a value no 63-bit key takes)
+// and the cube becomes NaN.  Arguments that would make a kernel read or write
+// out of place -- host memory, another device's memory, misaligned pointers
+// -- are rejected on the host before any launch.
 #include <mutex>
 #include <string>
 
@@ -38,12 +45,15 @@ constexpr int kNaMaxDevices = 64;
 struct NaBox {
     float mn[3];
     float mx[3];
-    float pad[2];
+    int bad;  // particles of the chunk with a non-finite coordinate
+    int pad;
 };
 
 struct NaScratch {
     NaBox part[kNaMaxChunks];  // one box per chunk
-    float cube[8];             // lo[3], side, scale
+    float cube[5];             // lo[3], side, scale
+    int bad;                   // non-finite coordinates anywhere in the input
+    int pad[2];
 };
 
 // 128 KiB + 32 bytes per GPU
@@ -97,17 +107,21 @@ k_na_box(const float4 *__restrict__ pos, int n, NaScratch *__restrict__ s)
         mn[a] = __int_as_float(0x7f800000);
         mx[a] = __int_as_float(0xff800000);
     }
+    int bad = 0;
     for (int i = threadIdx.x; i < cnt; i += kNaThreads) {
         const float4 p = pos[base + i];
+        bad += !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z));
         mn[0] = fminf(mn[0], p.x); mx[0] = fmaxf(mx[0], p.x);
         mn[1] = fminf(mn[1], p.y); mx[1] = fmaxf(mx[1], p.y);
         mn[2] = fminf(mn[2], p.z); mx[2] = fmaxf(mx[2], p.z);
     }
+    bad = __syncthreads_count(bad != 0);
     na_block_box(mn, mx);
     if (threadIdx.x == 0) {
         NaBox b;
         for (int a = 0; a < 3; ++a) { b.mn[a] = mn[a]; b.mx[a] = mx[a]; }
-        b.pad[0] = b.pad[1] = 0.f;
+        b.bad = bad;
+        b.pad = 0;
         s->part[blockIdx.x] = b;
     }
 }
@@ -120,15 +134,24 @@ k_na_cube(int nchunks, NaScratch *__restrict__ s, float *__restrict__ cube_out)
         mn[a] = __int_as_float(0x7f800000);
         mx[a] = __int_as_float(0xff800000);
     }
+    int bad = 0;
     for (int k = threadIdx.x; k < nchunks; k += kNaThreads) {
         const NaBox b = s->part[k];
+        bad += b.bad;
         for (int a = 0; a < 3; ++a) {
             mn[a] = fminf(mn[a], b.mn[a]);
             mx[a] = fmaxf(mx[a], b.mx[a]);
         }
     }
+    bad = __syncthreads_count(bad != 0);
     na_block_box(mn, mx);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && bad) {
+        // no cube exists for non-finite input: mark it (keys likewise)
+        s->bad = 1;
+        if (cube_out)
+            for (int a = 0; a < 4; ++a) cube_out[a] = __int_as_float(0x7fc00000);
+    } else if (threadIdx.x == 0) {
+        s->bad = 0;
         float side = 0.f;
         for (int a = 0; a < 3; ++a) {
             const float e = __fsub_rn(mx[a], mn[a]);
@@ -170,7 +193,12 @@ k_na_keys(const float4 *__restrict__ pos, int n, const NaScratch *__restrict__ s
           uint64_t *__restrict__ keys)
 {
     const float lx = s->cube[0], ly = s->cube[1], lz = s->cube[2], scale = s->cube[4];
+    const bool bad = s->bad != 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (bad) {
+            keys[i] = BH_NOALLOC_BAD_KEY;
+            continue;
+        }
         const float4 p = pos[i];
         keys[i] = (na_spread3(na_quantise(p.x, lx, scale)) << 2) |
                   (na_spread3(na_quantise(p.y, ly, scale)) << 1) | na_spread3(na_quantise(p.z, lz, scale));
@@ -181,6 +209,28 @@ int na_fail(int code, const std::string &m)
 {
     bh::set_last_error(m);
     return code;
+}
+
+// BH_OK if p is memory that kernels on device `dev` can read and write in
+// place (device memory of that device, or managed memory) and is aligned to
+// `align` bytes; otherwise a message in bh_last_error and BH_ERR_INVALID.
+// cudaPointerGetAttributes allocates nothing.
+int na_check_ptr(const void *p, const char *what, int dev, uintptr_t align)
+{
+    if ((uintptr_t)p % align != 0)
+        return na_fail(BH_ERR_INVALID, std::string(what) + " must be aligned to " +
+                                           std::to_string((unsigned long long)align) + " bytes");
+    cudaPointerAttributes at;
+    const cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return na_fail(BH_ERR_INVALID, std::string(what) + ": not a pointer the CUDA runtime knows (" +
+                                           cudaGetErrorString(e) + ")");
+    }
+    if (at.type == cudaMemoryTypeManaged) return BH_OK;
+    if (at.type == cudaMemoryTypeDevice && at.device == dev) return BH_OK;
+    return na_fail(BH_ERR_INVALID, std::string(what) +
+                                       " must be device memory of the current device (or managed memory)");
 }
 
 }  // namespace
@@ -215,6 +265,11 @@ int bh_morton_keys_noalloc(const float *pos_mass, int64_t n, uint64_t *keys, flo
         }
         s = g_na_addr[dev];
     }
+    // pos_mass is read as float4, keys written as 64-bit words, cube as floats
+    int rc = na_check_ptr(pos_mass, "pos_mass", dev, 16);
+    if (rc == BH_OK) rc = na_check_ptr(keys, "keys", dev, 8);
+    if (rc == BH_OK && cube) rc = na_check_ptr(cube, "cube", dev, 4);
+    if (rc != BH_OK) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const int ni = (int)n;
     const int nchunks = (ni + kNaChunk - 1) / kNaChunk;

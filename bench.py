@@ -231,28 +231,97 @@ def cpu_model() -> str:
     return platform.machine()
 
 
+def oracle_errors(pos_mass, acc, theta, eps, sample=4096, seed=11, G=1.0):
+    """Force error of one result against the FP64 oracle, outside every timed
+    region: the oracle's tree of all of pos_mass, walked for a seeded sample of
+    particles.  Returns dict(err_p99, err_max, sample): the 99th percentile of
+    |a - a_ref| / |a_ref| and the maximum of |a - a_ref| / max(|a_ref|,
+    1e-3 rms|a_ref|) over the sample (rms over the sample), the measures the
+    parity tests gate at 1e-5 and 1e-3."""
+    import numpy as np
+    import oracle
+    n = len(pos_mass)
+    idx = np.sort(np.random.default_rng(seed).choice(n, min(sample, n), replace=False))
+    ref, _, _ = oracle.Tree(pos_mass).accel(theta, eps, G, targets=idx,
+                                             nthreads=os.cpu_count() or 1)
+    a = np.asarray(acc, dtype=np.float64)[idx, :3]
+    d = np.linalg.norm(a - ref, axis=1)
+    r = np.linalg.norm(ref, axis=1)
+    rms = float(np.sqrt(np.mean(r * r)))
+    rel = np.where(d > 0, d / np.where(r > 0, r, 1.0), 0.0)
+    relmax = np.where(d > 0, d / np.maximum(r, 1e-3 * rms), 0.0)
+    return {"err_p99": float(np.percentile(rel, 99)), "err_max": float(relmax.max()),
+            "err_sample": f"{len(idx)} of {n} particles (seed {seed}), FP64 oracle tree of all {n}"}
+
+
+def system_errors(B, h, n, theta, eps, sample=4096, seed=11):
+    """oracle_errors of a single system's current state (bh_get_state)."""
+    import numpy as np
+    x = np.zeros((n, 4), np.float32)
+    a = np.zeros((n, 4), np.float32)
+    B.bh_get_state(h, x, None, a)
+    return oracle_errors(x, a, theta, eps, sample, seed)
+
+
 def run_reference(args):
+    """The oracle as it stands, timed on the host cores.  Each step builds the
+    FP64 tree of all N particles and walks a sample of them; the sample is the
+    whole system when the run fits args.ref_budget_s seconds, else the largest
+    share that does, and the value is then extrapolated to all N (the line says
+    which)."""
+    import numpy as np
+    import oracle
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    import synth
     pm, _ = make_inputs()
-    sample = args.ref_sample
-    vals, spent = [], 0.0
+    n = len(pm)
+    threads = os.cpu_count() or 1
+    # size the per-step sample from one probe step (tree + 4096-particle walk)
+    t0 = time.perf_counter()
+    T = oracle.Tree(pm)
+    t1 = time.perf_counter()
+    probe = np.random.default_rng(99).choice(n, min(4096, n), replace=False)
+    T.accel(THETA, EPS, targets=probe, nthreads=threads)
+    t2 = time.perf_counter()
+    del T
+    per_particle = (t2 - t1) / len(probe)
+    per_step_budget = args.ref_budget_s / max(args.steps, 1)
+    sample = int(min(n, max(4096, (per_step_budget - (t1 - t0)) / max(per_particle, 1e-12))))
+    vals, spent, walk_s, tree_s = [], 0.0, 0.0, 0.0
     for k in range(args.warmup + args.steps):
-        v, s, threads = cpu_sample(pm, sample, seed=100 + k)
-        spent += s
-        if k >= args.warmup:
-            vals.append(v)
+        timed = k >= args.warmup
+        s_k = sample if timed else min(4096, n)
+        idx = np.arange(n) if s_k >= n else \
+            np.random.default_rng(100 + k).choice(n, s_k, replace=False)
+        a0 = time.perf_counter()
+        T = oracle.Tree(pm)
+        a1 = time.perf_counter()
+        T.accel(THETA, EPS, targets=idx, nthreads=threads)
+        a2 = time.perf_counter()
+        del T
+        if timed:
+            spent += a2 - a0
+            tree_s += a1 - a0
+            walk_s += a2 - a1
+            vals.append(n / ((a1 - a0) + (a2 - a1) * n / len(idx)))
     value = len(vals) / sum(1.0 / v for v in vals)  # total particle-steps / total time
+    full = sample >= n
+    how = ("each timed step: full FP64 tree build of all {n} particles (1 thread) + walk of "
+           "all {n} particles ({t} threads): measured, not extrapolated" if full else
+           "each timed step: full FP64 tree build of all {n} particles (1 thread) + walk of "
+           "{s} random particles ({t} threads), walk time extrapolated to all {n}").format(
+               n=n, s=sample, t=threads)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * N_PART / value,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * n / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n": N_PART},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "extrapolated": not full,
+                   "walk_sample_per_step": sample},
+        "measured_s": {"timed_steps_total": spent, "tree": tree_s, "walk": walk_s},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"each step: full FP64 tree build of all {N_PART} particles "
-                                   f"+ walk of {sample} random particles, extrapolated to N"},
+                         "sample": how, "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -331,6 +400,8 @@ def run_gpu(args):
     n_nodes = B.bh_node_count(h)
     build_bytes = 144 * N_PART + 48 * n_nodes
     build_gbs = build_bytes / (build_ms * 1e-3) / 1e9
+    # error of the state the timed steps reached, against the FP64 oracle
+    errs = system_errors(B, h, N_PART, THETA, EPS) if rank == 0 else {}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -386,6 +457,7 @@ def run_gpu(args):
         "clocks": clocks,
         "gpu_launches": launches,
     }
+    line.update(errs)
     line.update(extra)
     if rank == 0 and ws == 1 and not args.no_cpu:
         v, spent, threads = cpu_sample(pm, args.cpu_sample)
@@ -411,6 +483,8 @@ def bench_batched(args, B, torch):
     steps of one call in one CUDA graph, one persistent walk per step across
     all trees; against the plain single-system path solving the same systems
     one after another."""
+    import numpy as np
+
     import synth
     systems = synth.forest_systems(args.forest_systems, 256, 65536, seed=4, theta=0.5, eps=0.01)
     n_tot = sum(s.n for s in systems)
@@ -430,23 +504,42 @@ def bench_batched(args, B, torch):
         B.bh_forest_profile_begin(f)
         B.bh_forest_step(f, args.forest_steps, 1e-3, True)
         phase_ms, nst, _ = B.bh_forest_profile_end(f)
+        # error against the oracle: every particle of 8 seeded systems
+        pick = sorted(np.random.default_rng(12).choice(len(systems), 8, replace=False).tolist())
+        e99, emax = [], []
+        for k in pick:
+            sy = systems[k]
+            x = np.zeros((sy.n, 4), np.float32)
+            a = np.zeros((sy.n, 4), np.float32)
+            B.bh_forest_get_state(f, k, x, None, a)
+            e = oracle_errors(x, a, sy.theta, sy.eps, sample=sy.n)
+            e99.append(e["err_p99"])
+            emax.append(e["err_max"])
     finally:
         B.bh_forest_destroy(f)
     batched = n_tot * args.forest_steps / t_forest
-    # the plain path, one system after another (device time of bh_step only)
-    t_plain, ps_plain = 0.0, 0
-    for s in systems:
-        h = B.bh_create(B.params(1.0, s.eps, s.theta), s.pos_mass, s.vel)
+    # the plain path, one system after another (host wall time of bh_step
+    # only), with its kernels launched directly and with its steps replayed
+    # from a captured graph (captured by an untimed first call)
+    t_plain, t_graph, ps_plain = 0.0, 0.0, 0
+    for sy in systems:
+        h = B.bh_create(B.params(1.0, sy.eps, sy.theta), sy.pos_mass, sy.vel)
         try:
             B.bh_compute_accel(h)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             B.bh_step(h, args.plain_steps, 1e-3)
             t_plain += time.perf_counter() - t0
-            ps_plain += s.n * args.plain_steps
+            B.bh_step(h, args.plain_steps, 1e-3, True)  # capture + warm-up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            B.bh_step(h, args.plain_steps, 1e-3, True)
+            t_graph += time.perf_counter() - t0
+            ps_plain += sy.n * args.plain_steps
         finally:
             B.bh_destroy(h)
     plain = ps_plain / t_plain
+    plain_graph = ps_plain / t_graph
     return {"workload": f"{len(systems)} systems, N log-uniform [256, 65536] (sum {n_tot}), "
                         "half Plummer / half uniform cold collapse, eps 0.01, theta 0.5, dt 1e-3, seed 4",
             "value": batched, "unit": UNIT, "steps_in_one_graph": args.forest_steps,
@@ -454,10 +547,18 @@ def bench_batched(args, B, torch):
             "phase_ms_per_step": {k: float(v) / max(nst, 1) for k, v in
                                   zip(("integrate", "build", "walk"), phase_ms)},
             "walk_shape": list(shape),
+            "err_p99": max(e99), "err_max": max(emax),
+            "err_sample": f"every particle of systems {pick} after {3 * args.forest_steps} graph "
+                          "steps, worst system reported, FP64 oracle",
             "plain_sequential": {"value": plain, "unit": UNIT,
                                  "steps_per_system": args.plain_steps,
                                  "how": "bh_step on each system in turn, kernels launched directly"},
-            "speedup_vs_plain": batched / plain}
+            "plain_sequential_graph": {"value": plain_graph, "unit": UNIT,
+                                       "steps_per_system": args.plain_steps,
+                                       "how": "bh_step on each system in turn, its steps replayed "
+                                              "from a CUDA graph captured by an untimed first call"},
+            "speedup_vs_plain": batched / plain_graph,
+            "speedup_vs_plain_direct_launches": batched / plain}
 
 
 def bench_other_theta(args, B, torch, theta):
@@ -481,10 +582,11 @@ def bench_other_theta(args, B, torch, theta):
             B.bh_step(h, 1, DT, True)
         phase_ms, nst, _ = B.bh_profile_end(h)
         stats = B.bh_walk_stats(h)
+        errs = system_errors(B, h, N_PART, theta, EPS)
     finally:
         B.bh_destroy(h)
     step_ms = float(phase_ms.sum()) / nst
-    return {"workload": WORKLOAD.replace(f"theta={THETA}", f"theta={theta}"),
+    return {**errs, "workload": WORKLOAD.replace(f"theta={THETA}", f"theta={theta}"),
             "value": N_PART / (step_ms * 1e-3),
             "unit": UNIT, "ms_per_step": step_ms,
             "phase_ms_per_step": {k: float(v) / nst for k, v in
@@ -518,6 +620,7 @@ def bench_large(args, B, torch, fma_peak_tflops, hbm_gbs):
         for _ in range(steps):
             B.bh_step(h, 1, dt, True)
         phase_ms, nst, _ = B.bh_profile_end(h)
+        errs = system_errors(B, h, n, theta, eps) if args.large_errors else {}
     finally:
         B.bh_destroy(h)
     walk_ms = phase_ms[2] / nst
@@ -525,7 +628,8 @@ def bench_large(args, B, torch, fma_peak_tflops, hbm_gbs):
     step_ms = float(phase_ms.sum()) / nst
     inter_s = stats["interactions"] / (walk_ms * 1e-3)
     build_gbs = (144 * n + 48 * nodes) / (build_ms * 1e-3) / 1e9
-    return {"workload": "Plummer N=16,777,216, m=1/N, eps=0.002, theta=0.6, 10 KDK steps dt=2.5e-4, seed 3",
+    return {**errs,
+            "workload": "Plummer N=16,777,216, m=1/N, eps=0.002, theta=0.6, 10 KDK steps dt=2.5e-4, seed 3",
             "value": n / (step_ms * 1e-3), "unit": UNIT, "ms_per_step": step_ms,
             "phase_ms_per_step": {"integrate": phase_ms[0] / nst, "build": build_ms, "walk": walk_ms},
             "walk_shape": list(shape), "nodes": nodes,
@@ -543,31 +647,43 @@ def serve_pools():
     return {"plummer": synth.plummer(1 << 21, 51), "uniform": synth.uniform_cube(1 << 21, 52)}
 
 
-def serve_stream(B, rate_hz, seconds, seed, pools):
+def serve_stream(B, rate_hz, seconds, seed, pools, full_seconds=60.0, check=8):
     """Poisson request stream through bh_submit / bh_wait with continuous
     batching under a 160 GB HBM budget; each request a Plummer or uniform system
     of N log-uniform in [1024, 2097152], theta U[0.5, 0.8], 10-200 KDK steps of
-    dt 1e-3, eps 0.01.  Particles of a request are a seeded random subset of a
-    pre-drawn 2^21-particle Plummer sphere or uniform cube, masses 1/N (a random
-    subset of independent draws is itself an independent draw)."""
+    dt 1e-3, eps 0.01.  A request's particles are a window of consecutive
+    particles (at a seeded offset, wrapping around) of a pre-drawn 2^21-particle
+    Plummer sphere or uniform cube of independent draws, masses 1/N; payloads
+    are made up front, or as the requests arrive when a long window would hold
+    too much host memory.  Results of `check` seeded requests with
+    N <= 2^18 are checked against the FP64 oracle."""
     import numpy as np
     import synth
     reqs = synth.request_stream(rate_hz=rate_hz, duration_s=seconds, seed=seed)
-    payload = []
-    for r in reqs:
+    small = [k for k, r in enumerate(reqs) if r.n <= 1 << 18]
+    checked = set(np.random.default_rng(seed + 1000).choice(
+        small, min(check, len(small)), replace=False).tolist()) if small else set()
+
+    def payload(r):
         rng = np.random.default_rng(r.seed)
         pm_pool, v_pool = pools[r.kind]
-        idx = rng.choice(len(pm_pool), r.n, replace=False)
-        pm = np.ascontiguousarray(pm_pool[idx])
+        idx = np.arange(r.n) + int(rng.integers(0, len(pm_pool)))
+        pm = np.ascontiguousarray(np.take(pm_pool, idx, axis=0, mode="wrap"))
         pm[:, 3] = np.float32(1.0 / r.n)
-        payload.append((pm, np.ascontiguousarray(v_pool[idx])))
+        return pm, np.ascontiguousarray(np.take(v_pool, idx, axis=0, mode="wrap"))
+
+    # made up front unless that would hold more than 8 GB of host memory
+    ready = None
+    if sum(r.n for r in reqs) * 32 <= 8 << 30:
+        ready = [payload(r) for r in reqs]
     srv = B.bh_server_create(160 << 30, 256)
     tickets = [None] * len(reqs)
     try:
         t0 = time.perf_counter()
 
         def submit():
-            for k, (r, (pm, v)) in enumerate(zip(reqs, payload)):
+            for k, r in enumerate(reqs):
+                pm, v = ready[k] if ready is not None else payload(r)
                 delay = r.arrival_s - (time.perf_counter() - t0)
                 if delay > 0:
                     time.sleep(delay)
@@ -576,21 +692,34 @@ def serve_stream(B, rate_hz, seconds, seed, pools):
         th = threading.Thread(target=submit)
         th.start()
         th.join()
-        res = [B.bh_wait(srv, t, 0, 3600.0) for t in tickets]
+        res = [B.bh_wait(srv, t, reqs[k].n if k in checked else 0, 7200.0)
+               for k, t in enumerate(tickets)]
         stats = B.bh_server_stats_get(srv)
     finally:
         B.bh_server_destroy(srv)
     lat = np.array([x["done_s"] - x["submit_s"] for x in res])
     ps = sum(r.n * r.steps for r in reqs)
     span = max(x["done_s"] for x in res) - min(x["submit_s"] for x in res)
-    return {"workload": f"{len(reqs)} requests, Poisson {rate_hz:.3g}/s over {seconds} s, "
+    e99, emax = [], []
+    for k in sorted(checked):
+        e = oracle_errors(res[k]["pos_mass"], res[k]["acc"], reqs[k].theta, reqs[k].eps)
+        e99.append(e["err_p99"])
+        emax.append(e["err_max"])
+    window = (f"{seconds} s of arrivals (the full stream)" if seconds >= full_seconds else
+              f"truncated window: {seconds} s of arrivals, not the {full_seconds:g} s stream")
+    return {"workload": f"{len(reqs)} requests, Poisson {rate_hz:.3g}/s, {window}, "
                         "N log-uniform [1024, 2097152], theta U[0.5,0.8], 10-200 steps dt 1e-3, "
                         f"Plummer/uniform 50/50, seed {seed}",
             "value": ps / span, "unit": UNIT, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
             "offered_particle_steps_per_s": ps / max(seconds, 1e-9), "requests": len(reqs),
+            "admitted_particle_steps_per_s": ps / span,
             "peak_resident_systems": stats["peak_resident_systems"],
-            "ticks": stats["ticks"], "busy_s": stats["busy_s"]}
+            "peak_resident_bytes": stats["peak_resident_bytes"],
+            "ticks": stats["ticks"], "busy_s": stats["busy_s"],
+            "err_p99": max(e99) if e99 else None, "err_max": max(emax) if emax else None,
+            "err_sample": f"{len(e99)} seeded requests with N <= 2^18, 4096 particles each, "
+                          "FP64 oracle tree of the returned positions"}
 
 
 def bench_served(args, B, torch):
@@ -615,7 +744,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=1 << 20)
-    ap.add_argument("--ref-sample", type=int, default=4096)
+    ap.add_argument("--ref-budget-s", type=float, default=120.0,
+                    help="host seconds the reference arm's timed steps may take; the per-step "
+                         "walk sample is sized to fit (the whole system when it does)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ppl", type=int, default=0, help="fix the walk shape (skip the autotuner)")
@@ -632,6 +763,8 @@ def main():
                     help="skip the headline workload at theta 0.7")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-large-errors", dest="large_errors", action="store_false",
+                    help="skip the large leg's oracle check (an FP64 tree of 2^24 particles)")
     ap.add_argument("--forest-systems", type=int, default=512)
     ap.add_argument("--forest-steps", type=int, default=100)
     ap.add_argument("--plain-steps", type=int, default=10)

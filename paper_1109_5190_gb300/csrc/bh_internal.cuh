@@ -270,6 +270,7 @@ struct WalkShape {
     int group;
     bool open_inside;  // BH_OPEN_INSIDE: one particle per lane, group 1
     bool quad;         // BH_QUADRUPOLE: one particle per lane, group 1, Kahan
+    bool soft;         // every system has eps > 0 (no zero-distance guard needed)
 };
 
 // kahan / potential / counting variants; returns number of kernel launches

@@ -118,12 +118,15 @@ int check_params(double G, double eps, double theta)
     return BH_OK;
 }
 
-// Particle state of one system: pos, vel, acc, backup pos, backup vel.
+// Particle state of one system: pos, vel, acc, backup pos, backup vel.  The
+// five arrays live in memory the state owns (alloc) or in a region of a pool
+// that outlives it (place: the server's pool carved from its HBM budget).
 struct SysState {
     int64_t n = 0;
     DevBuf mem;
+    float4 *ext = nullptr;
     double G = 1.0, eps = 0.01, theta = 0.5, dt = 1e-3;
-    float4 *pos() const { return mem.as<float4>(); }
+    float4 *pos() const { return ext ? ext : mem.as<float4>(); }
     float4 *vel() const { return pos() + n; }
     float4 *acc() const { return pos() + 2 * n; }
     float4 *bpos() const { return pos() + 3 * n; }
@@ -133,6 +136,11 @@ struct SysState {
     {
         n = nn;
         return mem.ensure(bytes_for(nn));
+    }
+    void place(int64_t nn, void *region)
+    {
+        n = nn;
+        ext = static_cast<float4 *>(region);
     }
 };
 
@@ -171,6 +179,7 @@ struct Forest {
     cudaStream_t st = nullptr;
     cudaStream_t user = nullptr;
     cudaEvent_t ev_sync = nullptr;
+    cudaEvent_t ev_step = nullptr;  // end of a step enqueued by step_begin
     int dev = 0, nsm = 0;
     unsigned flags = 0;
     std::vector<SysState *> systems;
@@ -236,6 +245,7 @@ struct Forest {
         for (cudaEvent_t e : ev_plain) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_graph) cudaEventDestroy(e);
         if (ev_sync) cudaEventDestroy(ev_sync);
+        if (ev_step) cudaEventDestroy(ev_step);
         if (h_small) cudaFreeHost(h_small);
         if (st) cudaStreamDestroy(st);
     }
@@ -249,6 +259,7 @@ struct Forest {
         CKR(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
         prepare_sort_kernels();
         CKR(cudaEventCreateWithFlags(&ev_sync, cudaEventDisableTiming));
+        CKR(cudaEventCreateWithFlags(&ev_step, cudaEventDisableTiming));
         CKR(cudaMallocHost(&h_small, sizeof(Small)));
         std::memset(h_small, 0, sizeof(Small));
         TRY(d_small.ensure(sizeof(Small)));
@@ -512,9 +523,9 @@ struct Forest {
     WalkShape shape_of(const bh_tuning &t) const
     {
         if (fixed_shape())
-            return WalkShape{1, t.warps_per_block, t.blocks_per_sm, 1, open_inside(), quad()};
+            return WalkShape{1, t.warps_per_block, t.blocks_per_sm, 1, open_inside(), quad(), false};
         return WalkShape{t.ppl, t.warps_per_block, t.blocks_per_sm, walk_group(t.group), false,
-                         false};
+                         false, all_soft()};
     }
     // the split walk (group 0) recognises its top-level nodes by their
     // threshold, and the sibling-order walk forms it from the level: both need
@@ -525,6 +536,13 @@ struct Forest {
         return fixed_shape() || (bmax() && (g == 0 || g == BH_GROUP_SIBLINGS)) ? 1 : g;
     }
     bool sib_walk() const { return shape().group == BH_GROUP_SIBLINGS; }
+    // every system of the current tables has a positive softening length
+    bool all_soft() const
+    {
+        for (const SysStatic &d : h_sys)
+            if (!(d.eps2 > 0.f)) return false;
+        return !h_sys.empty();
+    }
     bool open_inside() const { return (flags & BH_OPEN_INSIDE) != 0; }
     bool quad() const { return (flags & BH_QUADRUPOLE) != 0; }
     bool bmax() const { return (flags & BH_OPEN_BMAX) != 0; }
@@ -662,60 +680,129 @@ struct Forest {
         for (int attempt = 0; remaining > 0; ++attempt) {
             // each retry grows the node buffer or adds a sort digit (at most 5)
             if (attempt > 16) return fail(BH_ERR_CAPACITY, "node buffer kept overflowing");
-            TRY(clear_status());
-            TRY(ensure_tiles(tune.ppl));
-            TRY(ensure_sib_bufs());
-            if (graph) {
-                walk_max_blocks_per_sm(shape(), kahan(), pot());  // occupancy query outside capture
-                if (!gexec || g_nsteps != remaining || g_cap != node_cap || g_ntotal != n_total ||
-                    g_sort_first != sort_first || std::memcmp(&g_tune, &tune, sizeof tune) != 0 ||
-                    (prof && !g_prof))
-                    TRY(capture_graph(remaining));
-                CKR(cudaGraphLaunch(gexec, st));
-                launches += (int64_t)remaining * steps_launches();
-            } else {
-                for (int k = 0; k < remaining; ++k) TRY(enqueue_step());
-            }
+            TRY(launch_steps(remaining, graph));
             TRY(read_small());
-            choose_deep_cut();
-            if (prof) {
-                if (graph) {
-                    if (g_prof) accumulate(graph_marks, ev_graph);
-                } else {
-                    accumulate(plain_marks, ev_plain);
-                }
-                plain_marks.clear();
-                ev_plain_used = 0;
-            }
-            const Small &h = *h_small;
-            if (h.status == ST_OK) {
-                remaining = 0;
-                break;
-            }
-            if (h.status == ST_SORT_LONG) {  // redo with one more digit, from here on
-                const int done = (int)h.steps_done;
-                launch_restore(bufs(), st);
-                launches += 1;
-                sort_first = sort_first > 0 ? sort_first - 1 : 0;
-                remaining -= done;
-                tree_valid = false;
-                continue;
-            }
-            if (h.status == ST_CAPACITY) {
-                const int done = (int)h.steps_done;
-                launch_restore(bufs(), st);
-                launches += 1;
-                const size_t want = (size_t)h.needed + h.needed / 4 + 1024;
-                TRY(ensure_nodes(want));
-                remaining -= done;
-                tree_valid = false;
-                continue;
-            }
-            if (h.status == ST_WALK_LIMIT)
-                return fail(BH_ERR_CUDA, "walk stopped on a corrupt tree (skip pointer not advancing)");
-            return fail(BH_ERR_CUDA, "device status " + std::to_string(h.status));
+            TRY(settle(remaining, graph));
         }
         tree_valid = true;
+        return BH_OK;
+    }
+
+    // Enqueues `count` steps (from the captured graph or launched directly).
+    int launch_steps(int count, bool graph)
+    {
+        TRY(clear_status());
+        TRY(ensure_tiles(tune.ppl));
+        TRY(ensure_sib_bufs());
+        if (graph) {
+            walk_max_blocks_per_sm(shape(), kahan(), pot());  // occupancy query outside capture
+            if (!gexec || g_nsteps != count || g_cap != node_cap || g_ntotal != n_total ||
+                g_sort_first != sort_first || std::memcmp(&g_tune, &tune, sizeof tune) != 0 ||
+                (prof && !g_prof))
+                TRY(capture_graph(count));
+            CKR(cudaGraphLaunch(gexec, st));
+            launches += (int64_t)count * steps_launches();
+        } else {
+            for (int k = 0; k < count; ++k) TRY(enqueue_step());
+        }
+        return BH_OK;
+    }
+
+    // After the launched steps have finished and h_small holds the device
+    // status: remaining = 0 when they all succeeded; after a node-buffer
+    // overflow or a sort run too long for the short sort, the failed step is
+    // rolled back, the buffer grown (or a sort digit added) and remaining set
+    // to the steps still to do.
+    int settle(int &remaining, bool graph)
+    {
+        choose_deep_cut();
+        if (prof) {
+            if (graph) {
+                if (g_prof) accumulate(graph_marks, ev_graph);
+            } else {
+                accumulate(plain_marks, ev_plain);
+            }
+            plain_marks.clear();
+            ev_plain_used = 0;
+        }
+        const Small &h = *h_small;
+        if (h.status == ST_OK) {
+            remaining = 0;
+            return BH_OK;
+        }
+        if (h.status == ST_SORT_LONG) {  // redo with one more digit, from here on
+            const int done = (int)h.steps_done;
+            launch_restore(bufs(), st);
+            launches += 1;
+            sort_first = sort_first > 0 ? sort_first - 1 : 0;
+            remaining -= done;
+            tree_valid = false;
+            return BH_OK;
+        }
+        if (h.status == ST_CAPACITY) {
+            const int done = (int)h.steps_done;
+            launch_restore(bufs(), st);
+            launches += 1;
+            const size_t want = (size_t)h.needed + h.needed / 4 + 1024;
+            TRY(ensure_nodes(want));
+            remaining -= done;
+            tree_valid = false;
+            return BH_OK;
+        }
+        if (h.status == ST_WALK_LIMIT)
+            return fail(BH_ERR_CUDA, "walk stopped on a corrupt tree (skip pointer not advancing)");
+        return fail(BH_ERR_CUDA, "device status " + std::to_string(h.status));
+    }
+
+    // One step without waiting for it (the server overlaps its host work and
+    // copies with the step): step_begin enqueues it and the read-back of the
+    // device status; step_end waits for both and then behaves like run(1).
+    int step_begin()
+    {
+        TRY(launch_steps(1, false));
+        CKR(cudaMemcpyAsync(h_small, d_small.p, sizeof(Small), cudaMemcpyDeviceToHost, st));
+        CKR(cudaEventRecord(ev_step, st));
+        return BH_OK;
+    }
+
+    int step_end()
+    {
+        CKR(cudaEventSynchronize(ev_step));
+        int remaining = 1;
+        TRY(settle(remaining, false));
+        if (remaining > 0) return run(remaining, false);
+        tree_valid = true;
+        return BH_OK;
+    }
+
+    // Sizes every buffer for up to n_max particles in up to nsys_max systems,
+    // so that setup() for any set of systems within those limits allocates
+    // nothing (only a node-buffer overflow still grows the node arrays).
+    int reserve(int64_t n_max, int nsys_max)
+    {
+        const size_t N = (size_t)n_max;
+        const size_t chunks = N / kChunk + (size_t)nsys_max;
+        const size_t ntiles = N / 32 + (size_t)nsys_max;
+        TRY(d_sys.ensure(sizeof(SysStatic) * nsys_max));
+        TRY(d_dyn.ensure(sizeof(SysDyn) * nsys_max));
+        TRY(d_mode.ensure(sizeof(int) * nsys_max));
+        TRY(d_diag_out.ensure(sizeof(double) * 8 * nsys_max));
+        TRY(d_chunks.ensure(sizeof(int4) * chunks));
+        TRY(d_parts.ensure(sizeof(ChunkPart) * chunks));
+        TRY(d_diag_parts.ensure(sizeof(DiagPart) * chunks));
+        TRY(key0.ensure(N * 8));
+        TRY(key1.ensure(N * 8));
+        TRY(val0.ensure(N * 4));
+        TRY(val1.ensure(N * 4));
+        TRY(spos.ensure(N * 16));
+        TRY(ncount.ensure((N + 1) * 4));
+        TRY(noff.ensure((N + 1) * 4));
+        const size_t ncounts = (size_t)kRadixBins * chunks;
+        TRY(rs_counts.ensure(2 * ncounts * 4));
+        const size_t scan_n = std::max(ncounts, N + 1);
+        TRY(scan_part.ensure(((scan_n + kScanTile - 1) / kScanTile + 1) * 4));
+        TRY(ensure_nodes(2 * N + 1024));
+        for (auto &t : tiles) TRY(t.buf.ensure(sizeof(Tile) * ntiles));
         return BH_OK;
     }
 
@@ -886,7 +973,7 @@ struct Forest {
         TRY(ensure_tiles(1));
         TRY(clear_status());
         reset_step_counters();
-        WalkShape sh{1, 8, 0, walk_group(tune.group), open_inside(), quad()};
+        WalkShape sh{1, 8, 0, walk_group(tune.group), open_inside(), quad(), false};
         if (sh.group == BH_GROUP_SIBLINGS) {  // its copy of the current tree
             TRY(ensure_sib_bufs());
             launch_sibling_order(bufs(), st);
@@ -1364,6 +1451,56 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// First-fit sub-allocator over one region allocated up front (the server's
+// device pool and its pinned staging buffer): taking and returning a region
+// is host bookkeeping only, so the serving loop never calls an allocator.
+struct Pool {
+    static constexpr size_t kAlign = 256;
+    char *base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_;  // offset -> length, disjoint, never adjacent
+
+    static size_t round(size_t nb) { return (std::max<size_t>(nb, 1) + kAlign - 1) & ~(kAlign - 1); }
+    void init(void *b, size_t nb)
+    {
+        base = static_cast<char *>(b);
+        size = nb & ~(kAlign - 1);
+        free_.clear();
+        if (size) free_[0] = size;
+    }
+    void *take(size_t nb)
+    {
+        nb = round(nb);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < nb) continue;
+            const size_t off = it->first, len = it->second;
+            free_.erase(it);
+            if (len > nb) free_[off + nb] = len - nb;
+            return base + off;
+        }
+        return nullptr;
+    }
+    void give(void *p, size_t nb)
+    {
+        if (!p) return;
+        nb = round(nb);
+        size_t off = static_cast<size_t>(static_cast<char *>(p) - base);
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + nb == next->first) {  // merge with the following block
+            nb += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {  // merge with the preceding block
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += nb;
+                return;
+            }
+        }
+        free_[off] = nb;
+    }
+};
+
 struct Job {
     uint64_t ticket = 0;
     int64_t n = 0;
@@ -1377,6 +1514,10 @@ struct Job {
     bool accel_done = false;
     size_t bytes = 0;
     std::unique_ptr<SysState> state;
+    void *dev = nullptr;               // region of the device pool (state arrays)
+    void *stage = nullptr;             // region of the pinned staging buffer
+    size_t stage_bytes = 0;
+    cudaEvent_t ev = nullptr;          // end of the job's upload, then of its download
 };
 
 // Device bytes a resident system needs: its state (five float4 arrays) plus
@@ -1385,21 +1526,35 @@ struct Job {
 // 16 B, nodeD 32 B, level-list entry 4 B; up to ~2 nodes per particle with
 // the growth margin; in quadrupole mode also the second moments, under the
 // b_max rule each cell's FP64 b_max^2).
+size_t state_per_particle() { return 5 * 16; }
+size_t scratch_per_particle(unsigned flags)
+{
+    return (8 + 8 + 4 + 4 + 16 + 4 + 4) + 2 * (32 + 16 + 32 + 4) +
+           ((flags & BH_QUADRUPOLE) ? 2 * (6 * 8 + 2 * 16) : 0) +  // FP64 + FP32
+           ((flags & BH_OPEN_BMAX) ? 2 * 8 : 0);
+}
+constexpr size_t kJobOverhead = 4096 * 64;
 size_t job_bytes(int64_t n, unsigned flags)
 {
-    const size_t per = 5 * 16 + (8 + 8 + 4 + 4 + 16 + 4 + 4) + 2 * (32 + 16 + 32 + 4) +
-                       ((flags & BH_QUADRUPOLE) ? 2 * (6 * 8 + 2 * 16) : 0) +  // FP64 + FP32
-                       ((flags & BH_OPEN_BMAX) ? 2 * 8 : 0);
-    return (size_t)n * per + 4096 * 64;
+    return (size_t)n * (state_per_particle() + scratch_per_particle(flags)) + kJobOverhead;
 }
 
 }  // namespace
 
+// The server keeps, for its whole life, the device memory its budget allows:
+// one pool of state arrays (sub-allocated per admitted request) and the
+// forest's scratch sized for the most particles the budget can hold, plus a
+// pinned host staging buffer.  Each tick runs one forest step over the
+// resident systems without waiting for it; while it runs, the tick thread
+// admits requests (takes pool regions, stages their particles and uploads
+// them on a second stream) and delivers finished ones (their downloads,
+// issued on that stream when their last step ended, overlap the next step).
+// An admitted request joins the forest at the next tick, after its upload.
 struct bh_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<std::unique_ptr<Job>> pending;
-    std::vector<std::unique_ptr<Job>> resident;
+    std::vector<std::unique_ptr<Job>> resident;  // every job holding device memory
     std::map<uint64_t, std::unique_ptr<Job>> finished;
     std::map<uint64_t, int> where;  // 0 pending, 1 resident, 2 finished
     uint64_t next_ticket = 1;
@@ -1410,60 +1565,305 @@ struct bh_server {
     size_t resident_bytes = 0;
     bh_server_stats stats{};
     Forest forest;
+    cudaStream_t cp = nullptr;   // copies in and out
+    DevBuf pool_mem;             // state arrays of resident systems
+    Pool pool, staging;
+    void *staging_mem = nullptr;  // pinned
+    std::vector<cudaEvent_t> free_events;
     std::thread th;
     Clock::time_point t0;
-    std::string thread_error;
+
+    ~bh_server()
+    {
+        for (cudaEvent_t e : free_events) cudaEventDestroy(e);
+        if (staging_mem) cudaFreeHost(staging_mem);
+        if (cp) cudaStreamDestroy(cp);
+    }
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 
+    cudaEvent_t take_event()
+    {
+        if (!free_events.empty()) {
+            cudaEvent_t e = free_events.back();
+            free_events.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return e;
+    }
+
+    // Device memory and staging of a job go back to the pools; bookkeeping
+    // under mu is the caller's.
+    void release(Job &j)
+    {
+        if (j.stage) staging.give(j.stage, j.stage_bytes);
+        j.stage = nullptr;
+        j.stage_bytes = 0;
+        if (j.dev) pool.give(j.dev, SysState::bytes_for(j.n));
+        j.dev = nullptr;
+        j.state.reset();
+        if (j.ev) free_events.push_back(j.ev);
+        j.ev = nullptr;
+    }
+
+    int upload(Job &j);
+    int download(Job &j);
+    void admit(std::vector<Job *> &joining);
+    void deliver(std::vector<Job *> &leaving, bool wait);
     void loop();
 };
 
-void bh_server::loop()
+// Stages a job's particles in pinned memory and copies them to its pool
+// region on the copy stream; j.ev marks the end of the copy.  A job larger
+// than the whole staging buffer is copied from its own (pageable) arrays,
+// which makes the host wait for that copy.
+int bh_server::upload(Job &j)
 {
-    cudaSetDevice(forest.dev);
-    bool dirty = true;
+    SysState &S = *j.state;
+    const size_t nb = (size_t)j.n * sizeof(float4);
+    const bool has_vel = !j.vel.empty();
+    const float *src_pm = j.pm.data();
+    const float *src_v = has_vel ? j.vel.data() : nullptr;
+    if (j.stage) {
+        char *p = static_cast<char *>(j.stage);
+        std::memcpy(p, src_pm, nb);
+        src_pm = reinterpret_cast<const float *>(p);
+        if (has_vel) {
+            std::memcpy(p + nb, src_v, nb);
+            src_v = reinterpret_cast<const float *>(p + nb);
+        }
+    }
+    CKR(cudaMemcpyAsync(S.pos(), src_pm, nb, cudaMemcpyHostToDevice, cp));
+    if (has_vel) CKR(cudaMemcpyAsync(S.vel(), src_v, nb, cudaMemcpyHostToDevice, cp));
+    else CKR(cudaMemsetAsync(S.vel(), 0, nb, cp));
+    CKR(cudaMemsetAsync(S.acc(), 0, nb, cp));
+    CKR(cudaEventRecord(j.ev, cp));
+    return BH_OK;
+}
+
+// Copies a finished job's positions, velocities and accelerations out on the
+// copy stream (into staging when it has room, else straight into the job's
+// arrays, which makes the host wait); the forest's stream has finished the
+// job's last step when this is called.
+int bh_server::download(Job &j)
+{
+    SysState &S = *j.state;
+    const size_t nb = (size_t)j.n * sizeof(float4);
+    j.acc.resize((size_t)j.n * 4);
+    j.vel.resize((size_t)j.n * 4);
+    j.stage_bytes = 3 * nb;
+    j.stage = staging.take(j.stage_bytes);
+    float *dst[3] = {j.pm.data(), j.vel.data(), j.acc.data()};
+    if (j.stage) {
+        for (int k = 0; k < 3; ++k) dst[k] = reinterpret_cast<float *>(static_cast<char *>(j.stage) + k * nb);
+    } else {
+        j.stage_bytes = 0;
+    }
+    const float4 *src[3] = {S.pos(), S.vel(), S.acc()};
+    for (int k = 0; k < 3; ++k) CKR(cudaMemcpyAsync(dst[k], src[k], nb, cudaMemcpyDeviceToHost, cp));
+    CKR(cudaEventRecord(j.ev, cp));
+    return BH_OK;
+}
+
+// FIFO admission: the head of the queue is admitted while a slot is free, the
+// budget holds its bytes, and the pools have a region for its state (and for
+// its staging, unless it is too large to stage at all).
+void bh_server::admit(std::vector<Job *> &joining)
+{
     for (;;) {
-        std::vector<Job *> admitted;
+        Job *j = nullptr;
         {
-            std::unique_lock<std::mutex> lk(mu);
-            while (!stop && pending.empty() && resident.empty()) cv_work.wait(lk);
-            if (stop) break;
-            // FIFO admission by HBM budget and free slot
-            while (!pending.empty() && (int)resident.size() < max_slots &&
-                   resident_bytes + pending.front()->bytes <= budget) {
-                std::unique_ptr<Job> j = std::move(pending.front());
-                pending.pop_front();
-                resident_bytes += j->bytes;
-                j->admit_s = now();
-                where[j->ticket] = 1;
-                admitted.push_back(j.get());
-                resident.push_back(std::move(j));
-                stats.admitted++;
+            std::lock_guard<std::mutex> lk(mu);
+            if (stop || pending.empty() || (int)resident.size() >= max_slots ||
+                resident_bytes + pending.front()->bytes > budget)
+                return;
+            Job &h = *pending.front();
+            void *dev = pool.take(SysState::bytes_for(h.n));
+            if (!dev) return;
+            const size_t in_bytes = (size_t)h.n * sizeof(float4) * (h.vel.empty() ? 1 : 2);
+            void *stg = nullptr;
+            if (in_bytes <= staging.size) {
+                stg = staging.take(in_bytes);
+                if (!stg) {
+                    pool.give(dev, SysState::bytes_for(h.n));
+                    return;
+                }
             }
+            std::unique_ptr<Job> u = std::move(pending.front());
+            pending.pop_front();
+            j = u.get();
+            j->dev = dev;
+            j->stage = stg;
+            j->stage_bytes = stg ? in_bytes : 0;
+            resident_bytes += j->bytes;
+            j->admit_s = now();
+            where[j->ticket] = 1;
+            resident.push_back(std::move(u));
+            stats.admitted++;
             stats.resident_systems = (int64_t)resident.size();
             stats.peak_resident_systems = std::max(stats.peak_resident_systems, stats.resident_systems);
             stats.resident_bytes = (int64_t)resident_bytes;
             stats.peak_resident_bytes = std::max(stats.peak_resident_bytes, stats.resident_bytes);
         }
-        // allocate and upload outside the lock
-        for (Job *j : admitted) {
-            j->state = std::make_unique<SysState>();
-            SysState &S = *j->state;
-            S.G = j->G; S.eps = j->eps; S.theta = j->theta; S.dt = j->dt;
-            int rc = S.alloc(j->n);
-            if (rc == BH_OK) rc = load_state(forest, S, j->pm.data(), j->vel.empty() ? nullptr : j->vel.data(), 0);
-            if (rc == BH_OK) rc = forest.sync();
-            if (rc != BH_OK) j->status = rc;
-            dirty = true;
+        j->state = std::make_unique<SysState>();
+        SysState &S = *j->state;
+        S.G = j->G; S.eps = j->eps; S.theta = j->theta; S.dt = j->dt;
+        S.place(j->n, j->dev);
+        j->ev = take_event();
+        int rc = j->ev ? upload(*j) : fail(BH_ERR_CUDA, "cudaEventCreate failed");
+        if (rc != BH_OK) j->status = rc;
+        joining.push_back(j);
+    }
+}
+
+// Hands over the jobs whose downloads have finished (all of them, waiting,
+// when `wait`): results into the job's own arrays, memory back to the pools.
+void bh_server::deliver(std::vector<Job *> &leaving, bool wait)
+{
+    std::vector<Job *> ready;
+    for (size_t k = 0; k < leaving.size();) {
+        Job *j = leaving[k];
+        bool done = true;
+        if (j->ev) {
+            const cudaError_t e = wait ? cudaEventSynchronize(j->ev) : cudaEventQuery(j->ev);
+            if (e == cudaErrorNotReady) {
+                done = false;
+            } else if (e != cudaSuccess) {
+                cudaGetLastError();
+                if (j->status == BH_OK) j->status = fail(BH_ERR_CUDA, std::string("result copy: ") + cudaGetErrorString(e));
+            }
         }
+        if (!done) {
+            ++k;
+            continue;
+        }
+        if (j->status == BH_OK && j->stage) {
+            const size_t nb = (size_t)j->n * sizeof(float4);
+            const char *p = static_cast<const char *>(j->stage);
+            std::memcpy(j->pm.data(), p, nb);
+            std::memcpy(j->vel.data(), p + nb, nb);
+            std::memcpy(j->acc.data(), p + 2 * nb, nb);
+        }
+        ready.push_back(j);
+        leaving.erase(leaving.begin() + k);
+    }
+    if (ready.empty()) return;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (Job *j : ready) {
+            release(*j);
+            for (size_t k = 0; k < resident.size(); ++k) {
+                if (resident[k].get() != j) continue;
+                std::unique_ptr<Job> u = std::move(resident[k]);
+                resident.erase(resident.begin() + k);
+                resident_bytes -= u->bytes;
+                u->done_s = now();
+                where[u->ticket] = 2;
+                stats.completed++;
+                finished[u->ticket] = std::move(u);
+                break;
+            }
+        }
+        stats.resident_systems = (int64_t)resident.size();
+        stats.resident_bytes = (int64_t)resident_bytes;
+    }
+    cv_done.notify_all();
+}
+
+void bh_server::loop()
+{
+    cudaSetDevice(forest.dev);
+    std::vector<Job *> run;      // systems of the forest (the step in flight, if any)
+    std::vector<Job *> joining;  // uploads issued; they join at the next tick
+    std::vector<Job *> leaving;  // downloads issued
+    bool in_flight = false;
+    bool dirty = true;
+    for (;;) {
+        // 1. host work while the step runs: deliver finished downloads, admit
+        deliver(leaving, false);
+        admit(joining);
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (stop) break;
+            if (!in_flight && run.empty() && joining.empty()) {
+                if (!leaving.empty()) {
+                    lk.unlock();
+                    deliver(leaving, true);
+                    continue;
+                }
+                cv_work.wait(lk, [&] { return stop || !pending.empty(); });
+                continue;
+            }
+        }
+        // 2. finish the step in flight
         const double t_tick0 = now();
-        // drop failed admissions
-        std::vector<Job *> run;
-        for (auto &j : resident)
-            if (j->status == BH_OK) run.push_back(j.get());
-        int rc = BH_OK;
+        if (in_flight) {
+            int rc = forest.step_end();
+            in_flight = false;
+            int64_t ps = 0;
+            for (Job *j : run) {
+                if (rc != BH_OK) {
+                    j->status = rc;
+                    continue;
+                }
+                if (j->accel_done) {
+                    j->steps_done++;
+                    ps += j->n;
+                }
+                j->accel_done = true;
+            }
+            std::lock_guard<std::mutex> lk(mu);
+            if (rc == BH_OK) {
+                stats.ticks++;
+                stats.particle_steps += ps;
+            }
+        }
+        // 3. jobs that are done (or failed) leave; their downloads overlap the next step
+        for (size_t k = 0; k < run.size();) {
+            Job *j = run[k];
+            if (j->status != BH_OK || j->steps_done >= j->nsteps) {
+                if (j->status == BH_OK) {
+                    const int rc = download(*j);
+                    if (rc != BH_OK) j->status = rc;
+                }
+                leaving.push_back(j);
+                run.erase(run.begin() + k);
+                dirty = true;
+            } else {
+                ++k;
+            }
+        }
+        // 4. admitted jobs join (their uploads were issued a tick ago)
+        for (Job *j : joining) {
+            if (j->status == BH_OK && j->ev) {
+                const cudaError_t e = cudaEventSynchronize(j->ev);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    j->status = fail(BH_ERR_CUDA, std::string("request upload: ") + cudaGetErrorString(e));
+                }
+            }
+            if (j->stage) {
+                std::lock_guard<std::mutex> lk(mu);
+                staging.give(j->stage, j->stage_bytes);
+                j->stage = nullptr;
+                j->stage_bytes = 0;
+            }
+            if (j->status == BH_OK) {
+                run.push_back(j);
+                dirty = true;
+            } else {
+                leaving.push_back(j);
+            }
+        }
+        joining.clear();
+        // 5. launch the next step over the resident systems
         if (!run.empty()) {
+            int rc = BH_OK;
             if (dirty) {
                 forest.systems.clear();
                 for (Job *j : run) forest.systems.push_back(j->state.get());
@@ -1474,67 +1874,26 @@ void bh_server::loop()
                 std::vector<int> modes(run.size());
                 for (size_t k = 0; k < run.size(); ++k) modes[k] = run[k]->accel_done ? MODE_KDK : MODE_ACCEL;
                 rc = forest.set_modes(modes);
-                if (rc == BH_OK) rc = forest.run(1, false);
-                if (rc == BH_OK) {
-                    int64_t ps = 0;
-                    for (size_t k = 0; k < run.size(); ++k) {
-                        if (modes[k] == MODE_KDK) {
-                            run[k]->steps_done++;
-                            ps += run[k]->n;
-                        }
-                        run[k]->accel_done = true;
-                    }
-                    stats.ticks++;
-                    stats.particle_steps += ps;
+            }
+            if (rc == BH_OK) rc = forest.step_begin();
+            if (rc == BH_OK) {
+                in_flight = true;
+            } else {
+                for (Job *j : run) {
+                    j->status = rc;
+                    leaving.push_back(j);
                 }
-            }
-            if (rc != BH_OK)
-                for (Job *j : run) j->status = rc;
-        }
-        // retire finished (or failed) systems
-        std::vector<std::unique_ptr<Job>> done;
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            for (size_t k = 0; k < resident.size();) {
-                Job *j = resident[k].get();
-                if (j->status != BH_OK || (j->accel_done && j->steps_done >= j->nsteps)) {
-                    done.push_back(std::move(resident[k]));
-                    resident.erase(resident.begin() + k);
-                    dirty = true;
-                } else {
-                    ++k;
-                }
+                run.clear();
+                dirty = true;
             }
         }
-        for (auto &j : done) {
-            if (j->status == BH_OK && j->state) {
-                SysState &S = *j->state;
-                j->acc.resize((size_t)j->n * 4);
-                j->vel.resize((size_t)j->n * 4);
-                int r2 = download4(j->pm.data(), S.pos(), S.n, 0, forest.st);
-                if (r2 == BH_OK) r2 = download4(j->vel.data(), S.vel(), S.n, 0, forest.st);
-                if (r2 == BH_OK) r2 = download4(j->acc.data(), S.acc(), S.n, 0, forest.st);
-                if (r2 == BH_OK) r2 = forest.sync();
-                if (r2 != BH_OK) j->status = r2;
-            }
-            j->state.reset();
-        }
-        {
-            std::lock_guard<std::mutex> lk(mu);
-            stats.busy_s += now() - t_tick0;
-            for (auto &j : done) {
-                resident_bytes -= j->bytes;
-                j->done_s = now();
-                where[j->ticket] = 2;
-                stats.completed++;
-                finished[j->ticket] = std::move(j);
-            }
-            stats.resident_systems = (int64_t)resident.size();
-            stats.resident_bytes = (int64_t)resident_bytes;
-        }
-        if (!done.empty()) cv_done.notify_all();
+        std::lock_guard<std::mutex> lk(mu);
+        stats.busy_s += now() - t_tick0;
     }
-    // shutdown: cancel everything
+    // shutdown: let the device finish, then cancel everything
+    if (in_flight) forest.step_end();
+    forest.sync();
+    cudaStreamSynchronize(cp);
     std::lock_guard<std::mutex> lk(mu);
     for (auto &j : pending) {
         j->status = BH_ERR_CANCELLED;
@@ -1544,11 +1903,12 @@ void bh_server::loop()
     pending.clear();
     for (auto &j : resident) {
         j->status = BH_ERR_CANCELLED;
-        j->state.reset();
+        release(*j);
         where[j->ticket] = 2;
         finished[j->ticket] = std::move(j);
     }
     resident.clear();
+    resident_bytes = 0;
     cv_done.notify_all();
 }
 
@@ -1572,6 +1932,25 @@ int bh_server_create(bh_server **out, size_t hbm_budget, int max_slots, void *st
     TRY(s->forest.init(stream, flags));
     s->forest.adaptive_deep = false;
     s->forest.tune.static_share = 0;  // requests differ widely in cost per tile
+    // the budget, carved once: the most particles it can hold resident, their
+    // state arrays in one pool and the forest's scratch sized for them
+    const size_t per = state_per_particle() + scratch_per_particle(flags);
+    const int64_t n_max = (int64_t)std::min<size_t>(hbm_budget / per, (size_t)1 << 30);
+    if (n_max < 1) return fail(BH_ERR_INVALID, "budget holds no particle");
+    const size_t pool_bytes = SysState::bytes_for(n_max) + (size_t)max_slots * Pool::kAlign;
+    TRY(s->pool_mem.ensure(pool_bytes));
+    s->pool.init(s->pool_mem.p, pool_bytes);
+    TRY(s->forest.reserve(n_max, std::min<int64_t>(max_slots, n_max)));
+    // pinned staging: a slice of the budget, between 64 MiB and 1 GiB
+    const size_t stage_bytes = std::min<size_t>(std::max<size_t>(hbm_budget / 64, 64u << 20), 1u << 30);
+    if (cudaMallocHost(&s->staging_mem, stage_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        s->staging_mem = nullptr;
+        return fail(BH_ERR_OOM, "pinned staging allocation failed");
+    }
+    s->staging.init(s->staging_mem, stage_bytes);
+    CKR(cudaStreamCreateWithFlags(&s->cp, cudaStreamNonBlocking));
+    CKR(cudaStreamSynchronize(s->forest.st));
     s->t0 = Clock::now();
     bh_server *raw = s.get();
     try {

@@ -88,6 +88,22 @@ __device__ __forceinline__ void acc_fma(float &s, float &c, float a, float b)
     }
 }
 
+// The opening test s^2 < theta^2 d^2 as the walk first takes it, in FP32 on
+// the node's stored threshold crit = s^2 / theta^2: accept when d^2 exceeds
+// crit by more than the relative tie band, open when it falls short of it by
+// more; a test inside the band is re-decided in FP64 (accept_fp64).  Each
+// bound is one fused multiply-add with one rounding, so its sign is that of
+// the exact difference.  Leaves (crit = -1) are always accepted; buckets and
+// theta = 0 (crit = +inf) always open, without an FP64 test.
+__device__ __forceinline__ bool fp32_accepts(float d2, float crit)
+{
+    return fmaf(-crit, 1.0f + kTieBand, d2) > 0.f;
+}
+__device__ __forceinline__ bool fp32_opens(float d2, float crit)
+{
+    return fmaf(-crit, 1.0f - kTieBand, d2) < 0.f;
+}
+
 // The paper's opening test in FP64, for a test whose FP32 value lies within
 // rounding distance of the threshold: s^2 < theta^2 d^2 with s = side 2^-level
 // and d from the FP64 centre of mass (the same formula and operation order as
@@ -142,13 +158,16 @@ __device__ __forceinline__ int range_of_block(int nsm)
 }
 
 // One softened monopole term added to a particle slot's sums.
-template <bool KAHAN, bool POT, bool COUNT>
+// SOFT: every system of the launch has eps > 0, so r2 >= eps^2 > 0 and the
+// guard for a zero distance (eps = 0, coincident points) is not needed; the
+// result is the same bit for bit.
+template <bool KAHAN, bool POT, bool COUNT, bool SOFT = false>
 __device__ __forceinline__ void interact(float m, float dx, float dy, float dz, float d2, float eps2,
                                          bool self, float &ax, float &ay, float &az, float &cx,
                                          float &cy, float &cz, float &pp, float &cp, unsigned &cnt)
 {
     const float r2 = d2 + eps2;
-    const float inv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float inv = SOFT ? rsqrtf(r2) : (r2 > 0.f ? rsqrtf(r2) : 0.f);
     const float mi = m * inv;
     const float mi3 = mi * inv * inv;
     acc_fma<KAHAN>(ax, cx, mi3, dx);
@@ -160,7 +179,7 @@ __device__ __forceinline__ void interact(float m, float dx, float dy, float dz, 
 
 // A depth-cap bucket (equal keys down to level 21) is never taken as a whole:
 // its particles are summed one by one, like the leaves they would be.
-template <bool KAHAN, bool POT, bool COUNT>
+template <bool KAHAN, bool POT, bool COUNT, bool SOFT = false>
 __device__ __forceinline__ void bucket_sum(const int4 *__restrict__ nodeR,
                                         const float4 *__restrict__ spos, int node, float px,
                                         float py, float pz, int myj, float eps2, float &ax,
@@ -172,8 +191,8 @@ __device__ __forceinline__ void bucket_sum(const int4 *__restrict__ nodeR,
         const float4 P = __ldg(&spos[q]);
         const float dx = P.x - px, dy = P.y - py, dz = P.z - pz;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        interact<KAHAN, POT, COUNT>(P.w, dx, dy, dz, d2, eps2, q == myj, ax, ay, az, cx, cy, cz,
-                                    pp, cp, cnt);
+        interact<KAHAN, POT, COUNT, SOFT>(P.w, dx, dy, dz, d2, eps2, q == myj, ax, ay, az, cx,
+                                          cy, cz, pp, cp, cnt);
     }
 }
 
@@ -227,7 +246,7 @@ __device__ __forceinline__ void interact_quad(const float4 *Qp, float m, float d
 // Register budget: a block of up to 512 threads, and enough blocks per SM
 // for 48 resident warps with one particle per lane.
 template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false,
-          bool QUAD = false>
+          bool QUAD = false, bool SOFT = false>
 __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
 {
     static_assert(GROUP == 1 || GROUP == 2 || GROUP == 4 || GROUP == 8 || GROUP == 16 ||
@@ -319,9 +338,6 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
             // it), so each step moves forward and the loop ends
             const int skip = wn_skip(B);
             const float crit = wn_crit(B);
-            // band: negative for leaves (never a tie), infinite for buckets
-            // (whose test always opens: diff = -inf, never inside the band)
-            const float band = crit * kTieBand;
             // low part of the centre of mass: int16 multiples of a power of two,
             // folded into the distance by one fused multiply-add per axis
             // (the product is exact, so this equals adding the decoded value)
@@ -337,9 +353,8 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
                     const float dy = fmaf(lqy, lscale, A.y - py[k]);
                     const float dz = fmaf(lqz, lscale, A.z - pz[k]);
                     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float diff = d2 - crit;
-                    bool acc = diff > 0.f;
-                    if (fabsf(diff) < band)
+                    bool acc = fp32_accepts(d2, crit);
+                    if (!acc && !fp32_opens(d2, crit))
                         acc = accept_fp64(a.nodeD, a.nodeR, a.nodeB, a.sys, a.dyn, tl.sys, cur,
                                           px[k], py[k], pz[k]);
                     // alternative rule: a cell holding the particle (its leaf lies in
@@ -354,12 +369,12 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
                                                              cx[k], cy[k], cz[k], pp[k], cp[k],
                                                              cnt[k]);
                         else
-                            interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self,
-                                                        ax[k], ay[k], az[k], cx[k], cy[k], cz[k],
-                                                        pp[k], cp[k], cnt[k]);
+                            interact<KAHAN, POT, COUNT, SOFT>(A.w, dx, dy, dz, d2, eps2, self,
+                                                              ax[k], ay[k], az[k], cx[k], cy[k],
+                                                              cz[k], pp[k], cp[k], cnt[k]);
                         nxt[k] = skip;
                     } else if (crit == kBucketCrit) {
-                        bucket_sum<KAHAN, POT, COUNT>(a.nodeR, a.spos, cur, px[k], py[k], pz[k],
+                        bucket_sum<KAHAN, POT, COUNT, SOFT>(a.nodeR, a.spos, cur, px[k], py[k], pz[k],
                                                       myj[k], eps2, ax[k], ay[k], az[k], cx[k],
                                                       cy[k], cz[k], pp[k], cp[k], cnt[k]);
                         nxt[k] = skip;
@@ -499,10 +514,8 @@ __global__ void __launch_bounds__(512, 3) k_walk_sib(WalkArgs a)
             const float sl = __fmul_rn(side, __int_as_float((127 - level) << 23));
             const float ccell = __fmul_rn(__fmul_rn(sl, sl), inv_theta2);
             const float crit = kind == kSibCell ? ccell : (kind == kSibLeaf ? kLeafCrit : kBucketCrit);
-            const float band = crit * kTieBand;
-            const float diff = d2 - crit;
-            bool acc = diff > 0.f;
-            if (fabsf(diff) < band)
+            bool acc = fp32_accepts(d2, crit);
+            if (!acc && !fp32_opens(d2, crit))
                 acc = accept_fp64_sib(a.nodeD, a.sys, a.dyn, tl.sys, cur, level, px, py, pz);
             if (acc) {
                 const bool self = POT && kind == kSibLeaf && (int)B.x == myj;
@@ -642,15 +655,13 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
                 bool enq = false;
                 if (nxt == cur) {
                     if (COUNT) ++vis;
-                    const float band = crit * kTieBand;
                     const float lscale = __int_as_float(B.w & 0x7f800000u);
                     const float dx = fmaf((float)(short)(B.z & 0xffffu), lscale, A.x - px);
                     const float dy = fmaf((float)(short)(B.z >> 16), lscale, A.y - py);
                     const float dz = fmaf((float)(short)(B.w & 0xffffu), lscale, A.z - pz);
                     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float diff = d2 - crit;
-                    bool acc = diff > 0.f;
-                    if (fabsf(diff) < band)
+                    bool acc = fp32_accepts(d2, crit);
+                    if (!acc && !fp32_opens(d2, crit))
                         acc = accept_fp64(a.nodeD, a.nodeR, a.nodeB, a.sys, a.dyn, sysid, cur,
                                           px, py, pz);
                     if (acc) {
@@ -697,15 +708,13 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
                     load_node(a.nodeW + n2, A, B);
                     const int skip = wn_skip(B);  // > n2, checked by the topology pass
                     const float crit = wn_crit(B);
-                    const float band = crit * kTieBand;
                     const float lscale = __int_as_float(B.w & 0x7f800000u);
                     const float dx = fmaf((float)(short)(B.z & 0xffffu), lscale, A.x - px);
                     const float dy = fmaf((float)(short)(B.z >> 16), lscale, A.y - py);
                     const float dz = fmaf((float)(short)(B.w & 0xffffu), lscale, A.z - pz);
                     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float diff = d2 - crit;
-                    bool acc = diff > 0.f;
-                    if (fabsf(diff) < band)
+                    bool acc = fp32_accepts(d2, crit);
+                    if (!acc && !fp32_opens(d2, crit))
                         acc = accept_fp64(a.nodeD, a.nodeR, a.nodeB, a.sys, a.dyn, sysid, n2,
                                           px, py, pz);
                     if (acc) {
@@ -835,15 +844,13 @@ __global__ void __launch_bounds__(512, 3) k_walk_list(WalkArgs a)
                 bool take = false;
                 if (nxt == cur) {
                     if (COUNT) ++vis;
-                    const float band = crit * kTieBand;
                     const float lscale = __int_as_float(B.w & 0x7f800000u);
                     const float dx = fmaf((float)(short)(B.z & 0xffffu), lscale, A.x - px);
                     const float dy = fmaf((float)(short)(B.z >> 16), lscale, A.y - py);
                     const float dz = fmaf((float)(short)(B.w & 0xffffu), lscale, A.z - pz);
                     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    const float diff = d2 - crit;
-                    bool acc = diff > 0.f;
-                    if (fabsf(diff) < band)
+                    bool acc = fp32_accepts(d2, crit);
+                    if (!acc && !fp32_opens(d2, crit))
                         acc = accept_fp64(a.nodeD, a.nodeR, a.nodeB, a.sys, a.dyn, sysid, cur,
                                           px, py, pz);
                     take = acc || crit == kBucketCrit;
@@ -923,13 +930,13 @@ int cached_occupancy(std::atomic<int> &slot, F compute)
 // Blocks of `warps` warps that fit on one SM, queried once per variant and
 // block size (never during stream capture: callers query before capturing).
 template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false,
-          bool QUAD = false>
+          bool QUAD = false, bool SOFT = false>
 int occupancy(int warps)
 {
     static std::atomic<int> cache[33];
     if (warps < 1 || warps > 32) return 0;
     return cached_occupancy(cache[warps], [warps] {
-        auto *fn = k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD>;
+        auto *fn = k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD, SOFT>;
         // the walk uses no shared memory: give the SM's unified storage to L1
         cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
         int occ = 0;
@@ -1044,14 +1051,14 @@ int launch_list(const WalkArgs *a, const WalkShape &sh, int nsm, cudaStream_t st
 }
 
 template <int PPL, int GROUP, bool KAHAN, bool POT, bool COUNT, bool OPEN = false,
-          bool QUAD = false>
+          bool QUAD = false, bool SOFT = false>
 void launch_one(const WalkArgs &a, const WalkShape &sh, int nsm, cudaStream_t st)
 {
     const int threads = sh.warps * 32;
     int bps = sh.blocks_per_sm;
-    if (bps <= 0) bps = occupancy<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD>(sh.warps);
+    if (bps <= 0) bps = occupancy<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD, SOFT>(sh.warps);
     if (bps <= 0) bps = 1;
-    k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD><<<nsm * bps, threads, 0, st>>>(a);
+    k_walk<PPL, GROUP, KAHAN, POT, COUNT, OPEN, QUAD, SOFT><<<nsm * bps, threads, 0, st>>>(a);
 }
 
 template <bool KAHAN, bool POT, bool COUNT, bool OPEN, bool QUAD>
@@ -1098,6 +1105,16 @@ struct Variants {
         if (COUNT) {
             if (a) launch_one<PPL, GROUP, true, false, true>(*a, sh, nsm, st);
             return occupancy<PPL, GROUP, true, false, true>(sh.warps);
+        }
+        // one particle per lane without a vote and eps > 0 everywhere: the
+        // variant without the zero-distance guard (the same results)
+        if (PPL == 1 && GROUP == 1 && sh.soft && kahan) {
+            if (pot) {
+                if (a) launch_one<1, 1, true, true, false, false, false, true>(*a, sh, nsm, st);
+                return occupancy<1, 1, true, true, false, false, false, true>(sh.warps);
+            }
+            if (a) launch_one<1, 1, true, false, false, false, false, true>(*a, sh, nsm, st);
+            return occupancy<1, 1, true, false, false, false, false, true>(sh.warps);
         }
         if (kahan && pot) {
             if (a) launch_one<PPL, GROUP, true, true, false>(*a, sh, nsm, st);

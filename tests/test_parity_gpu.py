@@ -5,6 +5,8 @@ Gates: Morton keys, sort order and node topology bit-exact; per-particle
 accelerations within p99 <= 1e-5 and max <= 1e-3 relative (see metrics.py);
 per-particle interaction counts (accepted cells + leaf particles) equal.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -105,6 +107,11 @@ def test_tree_bit_exact_and_accel(kind, n, seed):
             r2 = (d ** 2).sum(-1) + eps ** 2
             mag = (m[None, :] * np.sqrt((d ** 2).sum(-1)) / r2 ** 1.5).sum(1)
             e = np.linalg.norm(a[:, :3] - ref, axis=1) / mag
+            # the spec measure too, so the departure from it stays visible
+            e99, emax = accel_errors(a, ref)
+            print(f"collinear n={n}: relative p99 {e99:.3e}, max {emax:.3e} (gate 1e-5 / 1e-3 "
+                  f"not applied); against the sum of term sizes p99 {np.percentile(e, 99):.3e}, "
+                  f"max {e.max():.3e}")
             assert np.percentile(e, 99) <= 1e-6 and e.max() <= 1e-5, (np.percentile(e, 99), e.max())
         else:
             assert_accel_close(a, ref, what=f"{kind} n={n}")
@@ -414,6 +421,62 @@ def test_server_results_same_alone_and_in_mix():
         finally:
             B.bh_destroy(h)
         assert np.array_equal(out["pos_mass"], x) and np.array_equal(out["acc"], a)
+
+
+def test_served_results_against_oracle():
+    # Eight requests of mixed kind, theta in [0.5, 0.8] and N up to ~100k go
+    # through bh_submit, each twice: with its step count and with one step
+    # fewer.  There are fewer slots than requests, and half of them arrive
+    # while the first ones run, so they are admitted into a forest in flight.
+    # Every served acceleration is checked against the FP64 oracle's walk of
+    # the returned positions, and the last step against an FP64 KDK step from
+    # the state the same request reaches one step earlier (served results do
+    # not depend on the mix, so the twin's result is that state).
+    rng = np.random.default_rng(2024)
+    eps, dt = 0.01, 1e-3
+    specs = []
+    for k in range(8):
+        kind = "plummer" if k % 2 == 0 else "uniform"
+        n = int(round(np.exp(rng.uniform(np.log(3000), np.log(100_000)))))
+        if k == 0:
+            n = 100_000
+        theta = float(rng.uniform(0.5, 0.8))
+        nsteps = int(rng.integers(1, 4))
+        pm, vel = gen(kind, n, 300 + k)
+        specs.append(dict(pm=pm, vel=vel, theta=theta, nsteps=nsteps))
+    srv = B.bh_server_create(8 << 30, 3)
+    try:
+        def submit(sp):
+            return [B.bh_submit(srv, sp["pm"], sp["vel"], 1.0, eps, sp["theta"], dt, ns)
+                    for ns in (sp["nsteps"], sp["nsteps"] - 1)]
+        tickets = [submit(sp) for sp in specs[:4]]
+        t0 = time.time()
+        while B.bh_server_stats_get(srv)["ticks"] < 2 and time.time() - t0 < 60:
+            time.sleep(0.001)
+        st0 = B.bh_server_stats_get(srv)
+        tickets += [submit(sp) for sp in specs[4:]]
+        res = [[B.bh_wait(srv, t, len(sp["pm"]), 300.0) for t in ts]
+               for ts, sp in zip(tickets, specs)]
+        st = B.bh_server_stats_get(srv)
+    finally:
+        B.bh_server_destroy(srv)
+    assert st0["completed"] < 16 and st["completed"] == 16 and st["peak_resident_systems"] <= 3
+    for k, (sp, (out, prev)) in enumerate(zip(specs, res)):
+        assert out["status"] == 0 and out["steps_done"] == sp["nsteps"]
+        assert prev["status"] == 0 and prev["steps_done"] == sp["nsteps"] - 1
+        x1, v1, a1 = out["pos_mass"], out["vel"], out["acc"]
+        x0, v0, a0 = prev["pos_mass"], prev["vel"], prev["acc"]
+        for x, a, what in ((x0, a0, "one step earlier"), (x1, a1, "served")):
+            ref, _, _ = oracle.Tree(x).accel(sp["theta"], eps)
+            e99, emax = assert_accel_close(a, ref, what=f"request {k} {what}")
+            print(f"request {k} n={len(x)} theta={sp['theta']:.3f} {what}: "
+                  f"p99 {e99:.2e}, max {emax:.2e}")
+        vh = v0[:, :3].astype(np.float64) + 0.5 * dt * a0[:, :3]
+        xe = x0[:, :3].astype(np.float64) + dt * vh
+        assert np.abs(x1[:, :3] - xe).max() <= 4e-7 * (1 + np.abs(xe).max())
+        ve = vh + 0.5 * dt * a1[:, :3].astype(np.float64)
+        assert np.abs(v1[:, :3] - ve).max() <= 4e-7 * (1 + np.abs(ve).max())
+        assert np.array_equal(x1[:, 3], sp["pm"][:, 3])
 
 
 def test_server_admission_by_budget_and_slots():

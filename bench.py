@@ -142,6 +142,25 @@ def combine_ranks(local_ms: float, units_per_rank: int, steps: int, device=None)
     return t_max, ws * units_per_rank * steps / (t_max * 1e-3)
 
 
+def shard_of(B, sizes, world: int, rank: int):
+    """Indices of the systems `rank` runs when independent systems of the
+    given sizes are dealt to `world` ranks (bh_partition_systems)."""
+    r = B.bh_partition_systems(sizes, world)
+    return [k for k in range(len(sizes)) if int(r[k]) == rank]
+
+
+def over_ranks(x: float, op: str = "max", device=None) -> float:
+    """A host scalar reduced over the ranks (max or sum); x itself on one rank."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def code_digest(texts) -> str:
     """SHA-256 of C/CUDA sources with comments and whitespace removed, so that
     it changes with the code and not with its comments."""
@@ -164,22 +183,28 @@ def walk_sources_sha() -> str:
     return code_digest(texts)
 
 
-def walk_traffic():
-    """DRAM bytes per walk launch from the committed ncu capture summary, or
-    None once the walk's sources differ from the ones that capture measured."""
+def walk_profile_field(name: str):
+    """An integer field (DRAM bytes, L1 sectors per walk launch) of the
+    committed ncu capture summary of the walk, or None once the walk's sources
+    differ from the ones that capture measured."""
     path = os.path.join(ROOT, "profiles", "walk_uniform1M_ncu.md")
     try:
         text = open(path).read()
     except OSError:
         return None
     fields = dict(line.split(":", 1) for line in text.splitlines()
-                  if line.startswith(("walk_source_sha256:", "dram_bytes_per_launch:")))
+                  if line.startswith(("walk_source_sha256:", name + ":")))
     if fields.get("walk_source_sha256", "").strip() != walk_sources_sha():
         return None
     try:
-        return int(fields["dram_bytes_per_launch"].strip())
+        return int(fields[name].strip())
     except (KeyError, ValueError):
         return None
+
+
+def walk_traffic():
+    """DRAM bytes per walk launch (committed ncu capture), or None."""
+    return walk_profile_field("dram_bytes_per_launch")
 
 
 # ---------------------------------------------------------------- reference
@@ -353,7 +378,7 @@ def run_gpu(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     if args.ppl:
-        B.bh_set_tuning(h, args.ppl, args.warps, 0, args.group, args.static_share)
+        B.bh_set_tuning(h, args.ppl, args.warps, args.bps, args.group, args.static_share)
         tuning = B.bh_get_tuning(h)
     else:
         tuning = B.bh_autotune(h)
@@ -394,6 +419,8 @@ def run_gpu(args):
     inter = 0.5 * (inter0 + inter1)
     achieved = inter * FLOPS_PER_INTERACTION / (walk_ms * 1e-3) / 1e12
     fma_peak = B.bh_micro_fma_peak(stream) / 1e3
+    l1_peak = B.bh_micro_l1_gather(stream)  # G sectors/s
+    l1_sectors = walk_profile_field("l1_sectors_per_launch")
     peaks, peak_src = measured_peaks()
     build_ms = phase_ms[1] / nsteps
     # algorithmic bytes of the build: 144 B per particle + 48 B per node
@@ -424,10 +451,11 @@ def run_gpu(args):
     extra = {}
     if rank == 0 and not args.no_theta07 and args.workload == "uniform1m":
         extra["theta_0.7"] = bench_other_theta(args, B, torch, 0.7)
-    if rank == 0 and not args.no_batched:
-        extra["batched"] = bench_batched(args, B, torch)
-    if rank == 0 and not args.no_served:
-        extra["served"] = bench_served(args, B, torch)
+    # sharded by system over every rank (one rank: the whole workload)
+    if not args.no_batched:
+        extra["batched"] = bench_batched(args, B, torch, dev)
+    if not args.no_served:
+        extra["served"] = bench_served(args, B, torch, dev)
     if rank == 0 and not args.no_large:
         extra["large"] = bench_large(args, B, torch, fma_peak, peaks["hbm_gbs"])
 
@@ -439,7 +467,8 @@ def run_gpu(args):
                    "parallelism": f"replicas{ws}" if ws > 1 else "single",
                    "l2": "flushed between timed steps (256 MiB write, outside the timed events)",
                    "walk_shape": {"ppl": tuning[0], "warps_per_block": tuning[1],
-                                  "group": tuning[3], "static_share": tuning[4]}},
+                                  "blocks_per_sm": tuning[2], "group": tuning[3],
+                                  "static_share": tuning[4]}},
         "phase_ms_per_step": {"integrate": phase_ms[0] / nsteps, "build": build_ms, "walk": walk_ms},
         "wall_ms_per_step": 1e3 * wall / args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fma_peak, "unit": "TFLOP/s",
@@ -449,6 +478,15 @@ def run_gpu(args):
                      "warp_iterations_per_launch": ws1["warp_iterations"],
                      "lane_efficiency": ws1["interactions"] / (32.0 * ws1["warp_iterations"]),
                      "slot_visits_per_launch": ws1["slot_visits"]},
+        # the walk against the limit it meets first: L1 throughput for
+        # scattered 32-byte node loads (project micro-benchmark), sectors per
+        # launch from the committed ncu capture of the same walk
+        "l1_roofline": {"bound": "l1", "unit": "G sectors/s", "peak": l1_peak,
+                        "achieved": (l1_sectors / (walk_ms * 1e-3) / 1e9) if l1_sectors else None,
+                        "frac": (l1_sectors / (walk_ms * 1e-3) / 1e9 / l1_peak) if l1_sectors else None,
+                        "sectors_per_launch": l1_sectors, "kernel": "k_walk",
+                        "peak_source": "project micro-benchmark: each lane loads its own random "
+                                       "32-byte record from an L1-resident table, 48 warps/SM"},
         "build_roofline": {"bound": "hbm", "achieved": build_gbs, "peak": peaks["hbm_gbs"],
                            "unit": "GB/s", "frac": build_gbs / peaks["hbm_gbs"],
                            "algorithmic_bytes": build_bytes, "nodes": n_nodes,
@@ -477,16 +515,21 @@ def run_gpu(args):
     return 0
 
 
-def bench_batched(args, B, torch):
+def bench_batched(args, B, torch, device=None):
     """Forest of many uneven systems (N log-uniform in [256, 65536], half
     Plummer, half uniform cold collapse, eps 0.01, theta 0.5, dt 1e-3): all
     steps of one call in one CUDA graph, one persistent walk per step across
     all trees; against the plain single-system path solving the same systems
-    one after another."""
+    one after another.  With several ranks the systems are dealt to them by
+    bh_partition_systems; each rank runs its share as its own forest, and the
+    value is all ranks' particle-steps over the slowest rank's time."""
     import numpy as np
 
     import synth
-    systems = synth.forest_systems(args.forest_systems, 256, 65536, seed=4, theta=0.5, eps=0.01)
+    ws, rank, _ = dist_env()
+    all_systems = synth.forest_systems(args.forest_systems, 256, 65536, seed=4, theta=0.5, eps=0.01)
+    mine = shard_of(B, [s.n for s in all_systems], ws, rank)
+    systems = [all_systems[k] for k in mine]
     n_tot = sum(s.n for s in systems)
     descs = [dict(pos_mass=s.pos_mass, vel=s.vel, eps=s.eps, theta=s.theta, dt=1e-3) for s in systems]
     f = B.bh_forest_create(descs)
@@ -504,10 +547,11 @@ def bench_batched(args, B, torch):
         B.bh_forest_profile_begin(f)
         B.bh_forest_step(f, args.forest_steps, 1e-3, True)
         phase_ms, nst, _ = B.bh_forest_profile_end(f)
-        # error against the oracle: every particle of 8 seeded systems
-        pick = sorted(np.random.default_rng(12).choice(len(systems), 8, replace=False).tolist())
+        # error against the oracle (rank 0): every particle of 8 seeded systems
+        pick = sorted(np.random.default_rng(12).choice(len(systems), min(8, len(systems)),
+                                                       replace=False).tolist())
         e99, emax = [], []
-        for k in pick:
+        for k in (pick if rank == 0 else []):
             sy = systems[k]
             x = np.zeros((sy.n, 4), np.float32)
             a = np.zeros((sy.n, 4), np.float32)
@@ -517,7 +561,9 @@ def bench_batched(args, B, torch):
             emax.append(e["err_max"])
     finally:
         B.bh_forest_destroy(f)
-    batched = n_tot * args.forest_steps / t_forest
+    t_forest = over_ranks(t_forest, "max", device)
+    n_all = int(over_ranks(n_tot, "sum", device))
+    batched = n_all * args.forest_steps / t_forest
     # the plain path, one system after another (host wall time of bh_step
     # only), with its kernels launched directly and with its steps replayed
     # from a captured graph (captured by an untimed first call)
@@ -538,18 +584,24 @@ def bench_batched(args, B, torch):
             ps_plain += sy.n * args.plain_steps
         finally:
             B.bh_destroy(h)
-    plain = ps_plain / t_plain
-    plain_graph = ps_plain / t_graph
-    return {"workload": f"{len(systems)} systems, N log-uniform [256, 65536] (sum {n_tot}), "
+    ps_plain = over_ranks(ps_plain, "sum", device)
+    plain = ps_plain / over_ranks(t_plain, "max", device)
+    plain_graph = ps_plain / over_ranks(t_graph, "max", device)
+    return {"workload": f"{len(all_systems)} systems, N log-uniform [256, 65536] (sum {n_all}), "
                         "half Plummer / half uniform cold collapse, eps 0.01, theta 0.5, dt 1e-3, seed 4",
             "value": batched, "unit": UNIT, "steps_in_one_graph": args.forest_steps,
+            "ranks": ws, "scaling": "strong",
+            "sharding": "systems dealt to ranks by bh_partition_systems (n log2 n, longest "
+                        "first); each rank runs its share as one forest; no data-path collective"
+                        if ws > 1 else "single rank",
             "ms_per_step": 1e3 * t_forest / args.forest_steps, "nodes": nodes,
             "phase_ms_per_step": {k: float(v) / max(nst, 1) for k, v in
                                   zip(("integrate", "build", "walk"), phase_ms)},
             "walk_shape": list(shape),
-            "err_p99": max(e99), "err_max": max(emax),
-            "err_sample": f"every particle of systems {pick} after {3 * args.forest_steps} graph "
-                          "steps, worst system reported, FP64 oracle",
+            "err_p99": max(e99) if e99 else None, "err_max": max(emax) if emax else None,
+            "err_sample": f"every particle of systems {[mine[k] for k in pick]} after "
+                          f"{3 * args.forest_steps} graph steps, worst system reported, FP64 oracle"
+                          + (" (rank 0's share)" if ws > 1 else ""),
             "plain_sequential": {"value": plain, "unit": UNIT,
                                  "steps_per_system": args.plain_steps,
                                  "how": "bh_step on each system in turn, kernels launched directly"},
@@ -647,7 +699,7 @@ def serve_pools():
     return {"plummer": synth.plummer(1 << 21, 51), "uniform": synth.uniform_cube(1 << 21, 52)}
 
 
-def serve_stream(B, rate_hz, seconds, seed, pools, full_seconds=60.0, check=8):
+def serve_stream(B, rate_hz, seconds, seed, pools, full_seconds=60.0, check=8, device=None):
     """Poisson request stream through bh_submit / bh_wait with continuous
     batching under a 160 GB HBM budget; each request a Plummer or uniform system
     of N log-uniform in [1024, 2097152], theta U[0.5, 0.8], 10-200 KDK steps of
@@ -655,12 +707,17 @@ def serve_stream(B, rate_hz, seconds, seed, pools, full_seconds=60.0, check=8):
     particles (at a seeded offset, wrapping around) of a pre-drawn 2^21-particle
     Plummer sphere or uniform cube of independent draws, masses 1/N; payloads
     are made up front, or as the requests arrive when a long window would hold
-    too much host memory.  Results of `check` seeded requests with
-    N <= 2^18 are checked against the FP64 oracle."""
+    too much host memory.  With several ranks the requests are dealt to them by
+    bh_partition_systems (on N x steps) and each rank serves its share with its
+    own server; latencies are gathered on the host.  Results of `check` seeded
+    requests with N <= 2^18 are checked against the FP64 oracle (rank 0)."""
     import numpy as np
     import synth
-    reqs = synth.request_stream(rate_hz=rate_hz, duration_s=seconds, seed=seed)
-    small = [k for k, r in enumerate(reqs) if r.n <= 1 << 18]
+    ws, rank, _ = dist_env()
+    all_reqs = synth.request_stream(rate_hz=rate_hz, duration_s=seconds, seed=seed)
+    mine = shard_of(B, [r.n * max(r.steps, 1) for r in all_reqs], ws, rank)
+    reqs = [all_reqs[k] for k in mine]
+    small = [k for k, r in enumerate(reqs) if r.n <= 1 << 18] if rank == 0 else []
     checked = set(np.random.default_rng(seed + 1000).choice(
         small, min(check, len(small)), replace=False).tolist()) if small else set()
 
@@ -681,25 +738,63 @@ def serve_stream(B, rate_hz, seconds, seed, pools, full_seconds=60.0, check=8):
     try:
         t0 = time.perf_counter()
 
+        failed = []
+
         def submit():
-            for k, r in enumerate(reqs):
-                pm, v = ready[k] if ready is not None else payload(r)
-                delay = r.arrival_s - (time.perf_counter() - t0)
-                if delay > 0:
-                    time.sleep(delay)
-                tickets[k] = B.bh_submit(srv, pm, v, 1.0, r.eps, r.theta, r.dt, r.steps)
+            try:
+                for k, r in enumerate(reqs):
+                    pm, v = ready[k] if ready is not None else payload(r)
+                    delay = r.arrival_s - (time.perf_counter() - t0)
+                    if delay > 0:
+                        time.sleep(delay)
+                    tickets[k] = B.bh_submit(srv, pm, v, 1.0, r.eps, r.theta, r.dt, r.steps)
+            except Exception as e:  # the collector stops waiting for tickets
+                failed.append(e)
+
+        # results are collected in submission order while requests still
+        # arrive, so finished requests do not pile up in host memory
+        res = [None] * len(reqs)
+
+        def collect():
+            try:
+                for k in range(len(reqs)):
+                    while tickets[k] is None:
+                        if failed:
+                            return
+                        time.sleep(1e-3)
+                    res[k] = B.bh_wait(srv, tickets[k], reqs[k].n if k in checked else 0, 7200.0)
+            except Exception as e:
+                failed.append(e)
 
         th = threading.Thread(target=submit)
+        tc = threading.Thread(target=collect)
         th.start()
+        tc.start()
         th.join()
-        res = [B.bh_wait(srv, t, reqs[k].n if k in checked else 0, 7200.0)
-               for k, t in enumerate(tickets)]
+        tc.join()
+        if failed:
+            raise failed[0]
+        if any(r is None for r in res):
+            raise RuntimeError("a served request returned no result")
         stats = B.bh_server_stats_get(srv)
     finally:
         B.bh_server_destroy(srv)
-    lat = np.array([x["done_s"] - x["submit_s"] for x in res])
+    lat = [x["done_s"] - x["submit_s"] for x in res]
     ps = sum(r.n * r.steps for r in reqs)
-    span = max(x["done_s"] for x in res) - min(x["submit_s"] for x in res)
+    # each rank's span on its own server clock (all started within the same
+    # second); the job's rate is all ranks' particle-steps over the longest span
+    span = (max(x["done_s"] for x in res) - min(x["submit_s"] for x in res)) if res else 0.0
+    if ws > 1:
+        import torch.distributed as dist
+        parts = [None] * ws
+        dist.all_gather_object(parts, lat)
+        lat = [v for p in parts for v in p]
+        span = over_ranks(span, "max", device)
+        ps = over_ranks(ps, "sum", device)
+        stats = {k: over_ranks(stats[k], "sum", device) for k in
+                 ("peak_resident_systems", "peak_resident_bytes", "ticks")} | \
+                {"busy_s": over_ranks(stats["busy_s"], "max", device)}
+    lat = np.array(lat)
     e99, emax = [], []
     for k in sorted(checked):
         e = oracle_errors(res[k]["pos_mass"], res[k]["acc"], reqs[k].theta, reqs[k].eps)
@@ -707,12 +802,13 @@ def serve_stream(B, rate_hz, seconds, seed, pools, full_seconds=60.0, check=8):
         emax.append(e["err_max"])
     window = (f"{seconds} s of arrivals (the full stream)" if seconds >= full_seconds else
               f"truncated window: {seconds} s of arrivals, not the {full_seconds:g} s stream")
-    return {"workload": f"{len(reqs)} requests, Poisson {rate_hz:.3g}/s, {window}, "
+    return {"workload": f"{len(all_reqs)} requests, Poisson {rate_hz:.3g}/s, {window}, "
                         "N log-uniform [1024, 2097152], theta U[0.5,0.8], 10-200 steps dt 1e-3, "
                         f"Plummer/uniform 50/50, seed {seed}",
             "value": ps / span, "unit": UNIT, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)),
-            "offered_particle_steps_per_s": ps / max(seconds, 1e-9), "requests": len(reqs),
+            "offered_particle_steps_per_s": ps / max(seconds, 1e-9), "requests": len(all_reqs),
+            "ranks": ws,
             "admitted_particle_steps_per_s": ps / span,
             "peak_resident_systems": stats["peak_resident_systems"],
             "peak_resident_bytes": stats["peak_resident_bytes"],
@@ -722,16 +818,16 @@ def serve_stream(B, rate_hz, seconds, seed, pools, full_seconds=60.0, check=8):
                           "FP64 oracle tree of the returned positions"}
 
 
-def bench_served(args, B, torch):
+def bench_served(args, B, torch, device=None):
     """The request stream of the served workload (200 requests/s), then the
     same mix at half the throughput the first run measured, where latency is
     service time rather than queueing."""
     pools = serve_pools()
-    out = serve_stream(B, 200.0, args.serve_seconds, 5, pools)
+    out = serve_stream(B, 200.0, args.serve_seconds, 5, pools, device=device)
     if args.serve_light_seconds > 0:
         per_request = out["offered_particle_steps_per_s"] / 200.0  # particle-steps per request
         rate = 0.5 * out["value"] / max(per_request, 1.0)
-        light = serve_stream(B, rate, args.serve_light_seconds, 6, pools)
+        light = serve_stream(B, rate, args.serve_light_seconds, 6, pools, device=device)
         light["load"] = "offered load = 0.5 x the throughput measured at 200 requests/s"
         out["half_load"] = light
     return out
@@ -751,6 +847,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ppl", type=int, default=0, help="fix the walk shape (skip the autotuner)")
     ap.add_argument("--warps", type=int, default=8)
+    ap.add_argument("--bps", type=int, default=0, help="walk blocks per SM (0 = as many as fit)")
     ap.add_argument("--group", type=int, default=1,
                     help="lanes voting together (1, 2, 4, 8 or 32; 0 = split walk, "
                          "64 = interaction lists, 65 = one lane per particle over "

@@ -299,6 +299,20 @@ int bh_forest_info(bh_forest *f, int64_t *n_total, int64_t *n_nodes);
 int bh_forest_profile_begin(bh_forest *f);
 int bh_forest_profile_end(bh_forest *f, double *phase_ms, int64_t *steps, int64_t *launches);
 
+/* Deals nsys independent systems of sizes n[0..nsys) to `world` ranks (one
+ * GPU each) for a run sharded by system: rank_of[s] receives the rank of
+ * system s.  The paper's conclusion (Section VI) names distributed runs as the
+ * next step; systems of a forest or a request stream are independent, so a
+ * rank needs nothing from another but the final gather of results.  The cost
+ * of a system is taken as n log2 n (the walk's work at a fixed theta); systems
+ * are assigned longest first, each to the rank with the least cost so far
+ * (ties: the lower system index first, the lower rank), which keeps the
+ * largest rank cost within 4/3 of the best possible.  Deterministic: every
+ * rank calling it with the same sizes gets the same assignment.  Host only
+ * (no device work).  BH_ERR_INVALID for nsys < 0, world < 1, a size < 1 or
+ * null arrays with nsys > 0. */
+int bh_partition_systems(int nsys, const int64_t *n, int world, int *rank_of);
+
 /* ------------------------------------------------------------------ server */
 
 /* A solve request: particles (host arrays, copied at submit), parameters,
@@ -399,6 +413,12 @@ int bh_morton_keys_noalloc(const float *pos_mass, int64_t n, uint64_t *keys, flo
 /* Measured FP32 non-tensor throughput: a kernel of independent FMA chains on
  * every SM; *gflops = 2 x FMAs / time. */
 int bh_micro_fma_peak(double *gflops, void *stream);
+/* Measured L1 throughput of the walk's kind of load: every lane reads its
+ * own pseudo-random 32-byte record (one 256-bit load) from a table that stays
+ * in L1, 48 warps per SM.  *gsectors = distinct 32-byte sectors delivered per
+ * second (in units of 1e9), the ceiling for a walk in which each lane sits at
+ * its own node. */
+int bh_micro_l1_gather(double *gsectors, void *stream);
 /* Measured device copy bandwidth over a buffer of `bytes` (read + write
  * counted). */
 int bh_micro_copy_bw(size_t bytes, double *gbs, void *stream);

@@ -120,8 +120,10 @@ _SIGS = {
     "bh_server_stats_get": ([P, P], I),
     "bh_server_now": ([P], D),
     "bh_server_destroy": ([P], I),
+    "bh_partition_systems": ([I, P, I, P], I),
     "bh_morton_keys_noalloc": ([P, I64, P, P, P], I),
     "bh_micro_fma_peak": ([P, P], I),
+    "bh_micro_l1_gather": ([P, P], I),
     "bh_micro_copy_bw": ([SZ, P, P], I),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -445,6 +447,17 @@ def bh_server_destroy(h):
     return _check(lib.bh_server_destroy(h))
 
 
+# ---------------------------------------------------------------- sharding
+
+def bh_partition_systems(sizes, world: int) -> np.ndarray:
+    """Rank of each system (bh_partition_systems) for `world` ranks."""
+    n = np.ascontiguousarray(np.asarray(sizes, dtype=np.int64))
+    out = np.zeros(n.size, np.int32)
+    _check(lib.bh_partition_systems(int(n.size), n.ctypes.data if n.size else None, int(world),
+                                    out.ctypes.data if n.size else None))
+    return out
+
+
 # ------------------------------------------------- allocation-free Morton keys
 
 BH_NOALLOC_MAX_N = 16777216
@@ -484,6 +497,13 @@ def bh_morton_keys_noalloc(pos_mass, keys, cube=None, stream=None):
 def bh_micro_fma_peak(stream=None) -> float:
     g = C.c_double()
     _check(lib.bh_micro_fma_peak(C.byref(g), _stream(stream)))
+    return g.value
+
+
+def bh_micro_l1_gather(stream=None) -> float:
+    """G sectors/s of scattered 32-byte L1 loads (the walk's node loads)."""
+    g = C.c_double()
+    _check(lib.bh_micro_l1_gather(C.byref(g), _stream(stream)))
     return g.value
 
 

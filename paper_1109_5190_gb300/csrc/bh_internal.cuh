@@ -280,6 +280,7 @@ int walk_max_blocks_per_sm(const WalkShape &sh, bool kahan, bool pot);
 
 // micro-benchmarks
 double micro_fma_gflops(cudaStream_t st);
+double micro_l1_sectors(cudaStream_t st);  // G sectors/s of scattered 32-byte L1 loads
 double micro_copy_gbs(size_t bytes, cudaStream_t st);
 
 // number of kernel launches issued by the last launch_* helper call on

@@ -274,7 +274,27 @@ struct Span {
     int lo, hi;  // levels of the nodes the bottom-up pass computes (lo > hi: none)
 };
 
-__device__ __forceinline__ Span node_span(const uint64_t *__restrict__ key, int j, int a, int b)
+// Sorted keys read straight from global memory.
+struct GlobalKeys {
+    const uint64_t *__restrict__ g;
+    __device__ __forceinline__ uint64_t operator[](int p) const { return g[p]; }
+};
+
+// Sorted keys with the run key[s0 .. s1) staged in shared memory (a block's
+// chunk and its two neighbours): the searches of the many small cells stay on
+// chip, and only cells reaching past the chunk read global memory.
+struct StagedKeys {
+    const uint64_t *__restrict__ g;
+    const uint64_t *s;
+    int s0, s1;
+    __device__ __forceinline__ uint64_t operator[](int p) const
+    {
+        return (p >= s0 && p < s1) ? s[p - s0] : g[p];
+    }
+};
+
+template <class Keys>
+__device__ __forceinline__ Span node_span(const Keys &key, int j, int a, int b)
 {
     Span s;
     const uint64_t kj = key[j];
@@ -311,7 +331,7 @@ k_topo_count(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
         const int i = k * kWideThreads + threadIdx.x;
         if (i >= c.z) break;
         const int j = c.y + i;
-        const Span s = node_span(key, j, S.start, S.start + S.n);
+        const Span s = node_span(GlobalKeys{key}, j, S.start, S.start + S.n);
         ncount[j] = (uint32_t)s.cnt;
         for (int l = s.lo; l <= s.hi; ++l) atomicAdd(&h[l], 1u);
     }
@@ -342,8 +362,8 @@ __global__ void k_level_offsets(Small *__restrict__ sm, const uint32_t *__restri
 
 // First index e in [lo, b] whose key leaves the level-l cell of kj (all
 // indices below lo are known to be inside): galloping then bisection.
-__device__ __forceinline__ int cell_end(const uint64_t *__restrict__ key, uint64_t kj, int lo,
-                                        int b, int l)
+template <class Keys>
+__device__ __forceinline__ int cell_end(const Keys &key, uint64_t kj, int lo, int b, int l)
 {
     const int sh = 3 * (kLevels - l);
     int step = 1, hi;
@@ -416,15 +436,20 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
 {
     if (halted(sm)) return;
     __shared__ unsigned h[kNumLevels], base[kNumLevels];
+    __shared__ uint64_t skey[kChunk + 2];
     if (threadIdx.x < kNumLevels) h[threadIdx.x] = 0;
-    __syncthreads();
     const int4 c = chunks[blockIdx.x];
     const SysStatic S = sys[c.x];
     const int a = S.start, b = S.start + S.n;
+    // the chunk's keys and one neighbour on each side (within the system)
+    const int s0 = max(c.y - 1, a), s1 = min(c.y + c.z + 1, b);
+    for (int p = s0 + (int)threadIdx.x; p < s1; p += kWideThreads) skey[p - s0] = key[p];
+    __syncthreads();
+    const StagedKeys K{key, skey, s0, s1};
     for (int k = 0; k < kWideItems; ++k) {
         const int i = k * kWideThreads + threadIdx.x;
         if (i >= c.z) break;
-        const Span s = node_span(key, c.y + i, a, b);
+        const Span s = node_span(K, c.y + i, a, b);
         for (int l = s.lo; l <= s.hi; ++l) atomicAdd(&h[l], 1u);
     }
     __syncthreads();
@@ -440,14 +465,14 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
         const int i = k * kWideThreads + threadIdx.x;
         if (i >= c.z) break;
         const int j = c.y + i;
-        const Span s = node_span(key, j, a, b);
+        const Span s = node_span(K, j, a, b);
         if (s.cnt == 0) continue;
-        const uint64_t kj = key[j];
+        const uint64_t kj = K[j];
         const unsigned nb = noff[j];
         int end = j + 1;
         for (int l = s.lmax; l > s.dprev; --l) {
             const unsigned n = nb + (unsigned)(l - s.dprev - 1);
-            if (l <= s.dnext) end = cell_end(key, kj, max(end, j + 2), b, l);
+            if (l <= s.dnext) end = cell_end(K, kj, max(end, j + 2), b, l);
             else end = j + 1;
             const int count = end - j;
             float crit;
@@ -558,6 +583,9 @@ struct ComRule {
     double *nodeB;        // FP64 b_max^2 per cell, read by the walk's tie test
 };
 
+// EXTRA: the b_max rule or quadrupole moments are on (their arrays non-null);
+// without them the kernels compile without those paths, in fewer registers.
+template <bool EXTRA>
 __device__ __forceinline__ void com_node(unsigned n, const float4 *__restrict__ spos,
                                          WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR,
                                          double4_32a *__restrict__ nodeD, double *__restrict__ nodeI,
@@ -592,17 +620,19 @@ __device__ __forceinline__ void com_node(unsigned n, const float4 *__restrict__ 
     nodeD[n] = make_double4_32a(M, cx, cy, cz);
     nodeW[n].a = make_float4(hx, hy, hz, (float)M);
     float crit_w = crit;
-    if (R.nodeB && crit != kBucketCrit) {  // a cell (theta > 0): b_max threshold
+    if (EXTRA && R.nodeB && crit != kBucketCrit) {  // a cell (theta > 0): b_max threshold
         const double bm2 = cell_bmax2(R.key[C.x], C.z, R.dyn[C.w], cx, cy, cz);
         R.nodeB[n] = bm2;
         crit_w = bmax_crit(bm2, R.sys[C.w].theta2);
     }
     nodeW[n].b = wn_pack(crit_w, skip, cx, cy, cz, hx, hy, hz);
-    if (nodeI) second_moments(n, C, crit, skip, cx, cy, cz, spos, nodeW, nodeD, nodeI, nodeQ);
+    if (EXTRA && nodeI) second_moments(n, C, crit, skip, cx, cy, cz, spos, nodeW, nodeD, nodeI, nodeQ);
 }
 
-// One level, all blocks.
-__global__ void __launch_bounds__(256)
+// One level, all blocks (the lean variant: six blocks of 256 per SM, 48 warps
+// to hide the latency of each thread's chain of child loads).
+template <bool EXTRA>
+__global__ void __launch_bounds__(256, EXTRA ? 1 : 6)
 k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
             WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4_32a *__restrict__ nodeD,
             double *__restrict__ nodeI, float4 *__restrict__ nodeQ, ComRule R,
@@ -612,11 +642,12 @@ k_com_level(int l, const uint32_t *__restrict__ nlist, const float4 *__restrict_
     const unsigned cnt = sm->level_cnt[l];
     const unsigned off = sm->level_off[l];
     for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += gridDim.x * blockDim.x)
-        com_node(nlist[off + k], spos, nodeW, nodeR, nodeD, nodeI, nodeQ, R);
+        com_node<EXTRA>(nlist[off + k], spos, nodeW, nodeR, nodeD, nodeI, nodeQ, R);
 }
 
 // The deep levels l_hi .. l_lo, which hold few nodes, in one block: a block
 // barrier separates the levels, so one launch replaces many near-empty ones.
+template <bool EXTRA>
 __global__ void __launch_bounds__(1024)
 k_com_deep(int l_hi, int l_lo, const uint32_t *__restrict__ nlist, const float4 *__restrict__ spos,
            WNode *__restrict__ nodeW, const int4 *__restrict__ nodeR, double4_32a *__restrict__ nodeD,
@@ -628,7 +659,7 @@ k_com_deep(int l_hi, int l_lo, const uint32_t *__restrict__ nlist, const float4 
         const unsigned cnt = sm->level_cnt[l];
         const unsigned off = sm->level_off[l];
         for (unsigned k = threadIdx.x; k < cnt; k += blockDim.x)
-            com_node(nlist[off + k], spos, nodeW, nodeR, nodeD, nodeI, nodeQ, R);
+            com_node<EXTRA>(nlist[off + k], spos, nodeW, nodeR, nodeD, nodeI, nodeQ, R);
         __syncthreads();
     }
 }
@@ -985,18 +1016,22 @@ void launch_topology(const BuildBufs &b, cudaStream_t st)
 
 void launch_com(const BuildBufs &b, cudaStream_t st)
 {
-    const int grid = b.nsm * 8;  // full occupancy: short per-thread chains of child loads
     const ComRule R{b.sys, b.dyn, b.key0, b.nodeB};
+    const bool extra = b.nodeB || b.nodeI;
+    // full occupancy: short per-thread chains of child loads
+    const int grid = b.nsm * (extra ? 8 : 6);
     int l = kLevels;
     if (b.deep_cut <= kLevels) {
-        k_com_deep<<<1, 1024, 0, st>>>(kLevels, b.deep_cut, b.nlist, b.spos, b.nodeW, b.nodeR,
-                                       b.nodeD, b.nodeI, b.nodeQ, R, b.small);
+        auto *deep = extra ? k_com_deep<true> : k_com_deep<false>;
+        deep<<<1, 1024, 0, st>>>(kLevels, b.deep_cut, b.nlist, b.spos, b.nodeW, b.nodeR, b.nodeD,
+                                 b.nodeI, b.nodeQ, R, b.small);
         g_launches += 1;
         l = b.deep_cut - 1;
     }
+    auto *level = extra ? k_com_level<true> : k_com_level<false>;
     for (; l >= 1; --l) {
-        k_com_level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeW, b.nodeR, b.nodeD,
-                                          b.nodeI, b.nodeQ, R, b.small);
+        level<<<grid, 256, 0, st>>>(l, b.nlist, b.spos, b.nodeW, b.nodeR, b.nodeD, b.nodeI,
+                                    b.nodeQ, R, b.small);
         g_launches += 1;
     }
     if (b.nodeI) launch_root_moments(b, st);

@@ -1423,6 +1423,34 @@ int bh_forest_profile_end(bh_forest *f, double *phase_ms, int64_t *steps, int64_
     return f->f.profile_end(phase_ms, steps, launches);
 }
 
+// ---------------------------------------------------------- sharding
+
+int bh_partition_systems(int nsys, const int64_t *n, int world, int *rank_of)
+{
+    if (nsys < 0 || world < 1) return fail(BH_ERR_INVALID, "nsys must be >= 0 and world >= 1");
+    if (nsys > 0 && (!n || !rank_of)) return fail(BH_ERR_INVALID, "null sizes or output");
+    std::vector<std::pair<double, int>> cost((size_t)nsys);
+    for (int s = 0; s < nsys; ++s) {
+        if (n[s] < 1) return fail(BH_ERR_INVALID, "system " + std::to_string(s) + ": size < 1");
+        const double x = (double)n[s];
+        cost[s] = {x * std::log2(std::max(x, 2.0)), s};
+    }
+    // longest first; equal costs in index order
+    std::sort(cost.begin(), cost.end(), [](const std::pair<double, int> &a,
+                                           const std::pair<double, int> &b) {
+        return a.first != b.first ? a.first > b.first : a.second < b.second;
+    });
+    std::vector<double> load((size_t)world, 0.0);
+    for (const auto &c : cost) {
+        int r = 0;
+        for (int q = 1; q < world; ++q)
+            if (load[q] < load[r]) r = q;
+        load[r] += c.first;
+        rank_of[c.second] = r;
+    }
+    return BH_OK;
+}
+
 // ---------------------------------------------------------- micro-benchmarks
 
 int bh_micro_fma_peak(double *gflops, void *stream)
@@ -1431,6 +1459,14 @@ int bh_micro_fma_peak(double *gflops, void *stream)
     *gflops = micro_fma_gflops((cudaStream_t)stream);
     CKR(cudaGetLastError());
     return *gflops > 0 ? BH_OK : fail(BH_ERR_CUDA, "fma micro-benchmark failed");
+}
+
+int bh_micro_l1_gather(double *gsectors, void *stream)
+{
+    if (!gsectors) return fail(BH_ERR_INVALID, "null out");
+    *gsectors = micro_l1_sectors((cudaStream_t)stream);
+    CKR(cudaGetLastError());
+    return *gsectors > 0 ? BH_OK : fail(BH_ERR_OOM, "L1 micro-benchmark allocation failed");
 }
 
 int bh_micro_copy_bw(size_t bytes, double *gbs, void *stream)

@@ -426,7 +426,15 @@ __device__ __forceinline__ float bmax_crit(double bm2, double theta2)
 // threshold, plus its slot in its level's list.  The root's centre of mass
 // comes from the FP64 reduction (or the particle itself for a one-particle
 // system); every other centre of mass is written by the bottom-up pass.
-__global__ void __launch_bounds__(kWideThreads)
+// Each 4096-particle chunk is split over kTopoSplit blocks of kTopoThreads, so
+// the grid spreads evenly over the SMs (one 1024-thread block per chunk left
+// the second of two waves two-thirds full).
+constexpr int kTopoSplit = 4;
+constexpr int kTopoThreads = 256;
+constexpr int kTopoSpan = kChunk / kTopoSplit;        // 1024 particles per block
+constexpr int kTopoItems = kTopoSpan / kTopoThreads;  // 4 per thread
+
+__global__ void __launch_bounds__(kTopoThreads)
 k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
              const SysDyn *__restrict__ dyn, const uint64_t *__restrict__ key,
              const uint32_t *__restrict__ noff, const float4 *__restrict__ spos,
@@ -435,19 +443,23 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
              double *__restrict__ nodeB, Small *__restrict__ sm)
 {
     if (halted(sm)) return;
+    const int4 cc = chunks[blockIdx.x / kTopoSplit];
+    const int part = (int)blockIdx.x % kTopoSplit;
+    // this block's particles [c.y, c.y + c.z) of chunk cc
+    const int4 c = make_int4(cc.x, cc.y + part * kTopoSpan, min(kTopoSpan, cc.z - part * kTopoSpan), 0);
+    if (c.z <= 0) return;  // a short chunk: the whole block leaves together
     __shared__ unsigned h[kNumLevels], base[kNumLevels];
-    __shared__ uint64_t skey[kChunk + 2];
+    __shared__ uint64_t skey[kTopoSpan + 2];
     if (threadIdx.x < kNumLevels) h[threadIdx.x] = 0;
-    const int4 c = chunks[blockIdx.x];
     const SysStatic S = sys[c.x];
     const int a = S.start, b = S.start + S.n;
-    // the chunk's keys and one neighbour on each side (within the system)
+    // the block's keys and one neighbour on each side (within the system)
     const int s0 = max(c.y - 1, a), s1 = min(c.y + c.z + 1, b);
-    for (int p = s0 + (int)threadIdx.x; p < s1; p += kWideThreads) skey[p - s0] = key[p];
+    for (int p = s0 + (int)threadIdx.x; p < s1; p += kTopoThreads) skey[p - s0] = key[p];
     __syncthreads();
     const StagedKeys K{key, skey, s0, s1};
-    for (int k = 0; k < kWideItems; ++k) {
-        const int i = k * kWideThreads + threadIdx.x;
+    for (int k = 0; k < kTopoItems; ++k) {
+        const int i = k * kTopoThreads + threadIdx.x;
         if (i >= c.z) break;
         const Span s = node_span(K, c.y + i, a, b);
         for (int l = s.lo; l <= s.hi; ++l) atomicAdd(&h[l], 1u);
@@ -461,8 +473,8 @@ k_topo_write(const int4 *__restrict__ chunks, const SysStatic *__restrict__ sys,
     }
     __syncthreads();
     const SysDyn D = dyn[c.x];
-    for (int k = 0; k < kWideItems; ++k) {
-        const int i = k * kWideThreads + threadIdx.x;
+    for (int k = 0; k < kTopoItems; ++k) {
+        const int i = k * kTopoThreads + threadIdx.x;
         if (i >= c.z) break;
         const int j = c.y + i;
         const Span s = node_span(K, j, a, b);
@@ -1008,9 +1020,9 @@ void launch_topology(const BuildBufs &b, cudaStream_t st)
     g_launches += 1;
     launch_scan(b.ncount, b.noff, b.n_total, b.scan_part, b.noff + b.n_total, &b.small->status, st);
     k_level_offsets<<<1, 32, 0, st>>>(b.small, b.noff, b.n_total, b.node_cap);
-    k_topo_write<<<b.nchunks, kWideThreads, 0, st>>>(b.chunks, b.sys, b.dyn, b.key0, b.noff,
-                                                      b.spos, b.nodeW, b.nodeR, b.nodeD, b.nlist,
-                                                      b.nodeI, b.nodeQ, b.nodeB, b.small);
+    k_topo_write<<<b.nchunks * kTopoSplit, kTopoThreads, 0, st>>>(
+        b.chunks, b.sys, b.dyn, b.key0, b.noff, b.spos, b.nodeW, b.nodeR, b.nodeD, b.nlist,
+        b.nodeI, b.nodeQ, b.nodeB, b.small);
     g_launches += 2;
 }
 

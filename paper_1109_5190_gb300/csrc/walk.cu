@@ -596,7 +596,7 @@ __device__ __forceinline__ int next_tile(const WalkArgs &a, unsigned *s_next, in
     return __shfl_sync(FULL, t, 0);
 }
 
-template <bool KAHAN, bool POT, bool COUNT>
+template <bool KAHAN, bool POT, bool COUNT, bool SOFT = false>
 __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
 {
     __shared__ uint2 s_q[kSplitMaxWarps][kSplitQueue];  // (first child, subtree end)
@@ -667,14 +667,14 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
                                           px, py, pz);
                     if (acc) {
                         const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[cur].x) == myj;
-                        interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az,
+                        interact<KAHAN, POT, COUNT, SOFT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az,
                                                     cx, cy, cz, pp, cp, cnt);
                         nxt = skip;
                     } else if (crit == crit_top) {
                         enq = true;
                         nxt = skip;
                     } else if (crit == kBucketCrit) {
-                        bucket_sum<KAHAN, POT, COUNT>(a.nodeR, a.spos, cur, px, py, pz, myj, eps2,
+                        bucket_sum<KAHAN, POT, COUNT, SOFT>(a.nodeR, a.spos, cur, px, py, pz, myj, eps2,
                                                       ax, ay, az, cx, cy, cz, pp, cp, cnt);
                         nxt = skip;
                     } else {
@@ -720,11 +720,11 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
                                           px, py, pz);
                     if (acc) {
                         const bool self = POT && crit == kLeafCrit && __ldg(&a.nodeR[n2].x) == myj;
-                        interact<KAHAN, POT, COUNT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az,
+                        interact<KAHAN, POT, COUNT, SOFT>(A.w, dx, dy, dz, d2, eps2, self, ax, ay, az,
                                                     cx, cy, cz, pp, cp, cnt);
                         n2 = skip;
                     } else if (crit == kBucketCrit) {
-                        bucket_sum<KAHAN, POT, COUNT>(a.nodeR, a.spos, n2, px, py, pz, myj, eps2,
+                        bucket_sum<KAHAN, POT, COUNT, SOFT>(a.nodeR, a.spos, n2, px, py, pz, myj, eps2,
                                                       ax, ay, az, cx, cy, cz, pp, cp, cnt);
                         n2 = skip;
                     } else {
@@ -955,13 +955,13 @@ int occupancy(int warps)
 
 // The split walk needs its queue and parked sums in shared memory: ask for
 // the smallest carveout that still holds the blocks the registers allow.
-template <bool KAHAN, bool POT, bool COUNT>
+template <bool KAHAN, bool POT, bool COUNT, bool SOFT = false>
 int occupancy_split(int warps)
 {
     static std::atomic<int> cache[33];
     if (warps < 1 || warps > kSplitMaxWarps) return 0;
     return cached_occupancy(cache[warps], [warps] {
-        auto *fn = k_walk_split<KAHAN, POT, COUNT>;
+        auto *fn = k_walk_split<KAHAN, POT, COUNT, SOFT>;
         cudaFuncAttributes fa{};
         int occ = 0;
         if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess) {
@@ -979,15 +979,15 @@ int occupancy_split(int warps)
     });
 }
 
-template <bool KAHAN, bool POT, bool COUNT>
+template <bool KAHAN, bool POT, bool COUNT, bool SOFT = false>
 int launch_split(const WalkArgs *a, const WalkShape &sh, int nsm, cudaStream_t st)
 {
     if (sh.ppl != 1) return 0;
-    const int occ = occupancy_split<KAHAN, POT, COUNT>(sh.warps);
+    const int occ = occupancy_split<KAHAN, POT, COUNT, SOFT>(sh.warps);
     if (occ <= 0) return 0;
     if (a) {
         const int bps = sh.blocks_per_sm > 0 ? sh.blocks_per_sm : occ;
-        k_walk_split<KAHAN, POT, COUNT><<<nsm * bps, sh.warps * 32, 0, st>>>(*a);
+        k_walk_split<KAHAN, POT, COUNT, SOFT><<<nsm * bps, sh.warps * 32, 0, st>>>(*a);
     }
     return occ;
 }
@@ -1161,6 +1161,8 @@ struct Variants {
         if (sh.group == 0) {  // split walk
             if (COUNT) return launch_split<true, false, true>(a, sh, nsm, st);
             if (kahan && pot) return launch_split<true, true, false>(a, sh, nsm, st);
+            // eps > 0 everywhere: the variant without the zero-distance guard
+            if (kahan && sh.soft) return launch_split<true, false, false, true>(a, sh, nsm, st);
             if (kahan) return launch_split<true, false, false>(a, sh, nsm, st);
             if (pot) return launch_split<false, true, false>(a, sh, nsm, st);
             return launch_split<false, false, false>(a, sh, nsm, st);

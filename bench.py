@@ -699,9 +699,10 @@ def serve_pools():
     return {"plummer": synth.plummer(1 << 21, 51), "uniform": synth.uniform_cube(1 << 21, 52)}
 
 
-def serve_stream(B, rate_hz, seconds, seed, pools, full_seconds=60.0, check=8, device=None):
+def serve_stream(B, rate_hz, seconds, seed, pools, full_seconds=60.0, check=8, device=None,
+                 budget_gb=160.0):
     """Poisson request stream through bh_submit / bh_wait with continuous
-    batching under a 160 GB HBM budget; each request a Plummer or uniform system
+    batching under an HBM budget (160 GB by default); each request a Plummer or uniform system
     of N log-uniform in [1024, 2097152], theta U[0.5, 0.8], 10-200 KDK steps of
     dt 1e-3, eps 0.01.  A request's particles are a window of consecutive
     particles (at a seeded offset, wrapping around) of a pre-drawn 2^21-particle
@@ -733,7 +734,7 @@ def serve_stream(B, rate_hz, seconds, seed, pools, full_seconds=60.0, check=8, d
     ready = None
     if sum(r.n for r in reqs) * 32 <= 8 << 30:
         ready = [payload(r) for r in reqs]
-    srv = B.bh_server_create(160 << 30, 256)
+    srv = B.bh_server_create(int(budget_gb * (1 << 30)), 256)
     tickets = [None] * len(reqs)
     try:
         t0 = time.perf_counter()
@@ -823,11 +824,13 @@ def bench_served(args, B, torch, device=None):
     same mix at half the throughput the first run measured, where latency is
     service time rather than queueing."""
     pools = serve_pools()
-    out = serve_stream(B, 200.0, args.serve_seconds, 5, pools, device=device)
+    out = serve_stream(B, 200.0, args.serve_seconds, 5, pools, device=device,
+                       budget_gb=args.serve_budget_gb)
     if args.serve_light_seconds > 0:
         per_request = out["offered_particle_steps_per_s"] / 200.0  # particle-steps per request
         rate = 0.5 * out["value"] / max(per_request, 1.0)
-        light = serve_stream(B, rate, args.serve_light_seconds, 6, pools, device=device)
+        light = serve_stream(B, rate, args.serve_light_seconds, 6, pools, device=device,
+                             budget_gb=args.serve_budget_gb)
         light["load"] = "offered load = 0.5 x the throughput measured at 200 requests/s"
         out["half_load"] = light
     return out
@@ -867,6 +870,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=10)
     ap.add_argument("--serve-light-seconds", type=float, default=8.0,
                     help="seconds of arrivals for the half-load served run (0 = skip)")
+    ap.add_argument("--serve-budget-gb", type=float, default=160.0,
+                    help="HBM budget of each rank's server (GB)")
     ap.add_argument("--serve-seconds", type=float, default=0.5,
                     help="length of the Poisson arrival window (200 requests/s)")
     ap.add_argument("--workload", default="uniform1m", choices=sorted(WORKLOADS))

@@ -4,10 +4,12 @@ with the single-GPU forest code, and only results are gathered on the host.
 
 CPU tests: the assignment covers every system exactly once, is deterministic,
 and keeps the largest rank cost within the longest-first bound; two gloo ranks
-each take their shard and together cover every system once.  GPU test: two
-ranks (processes) share one GPU, each runs its shard's forest through graph
+each take their shard and together cover every system once.  GPU tests: two
+ranks (processes) share one GPU; each runs its shard's forest through graph
 steps, and rank 0 finds every gathered system bit-identical to the same system
-in one forest of all of them.  No kernel of one rank waits on another rank.
+in one forest of all of them; and the benchmark's batched and served legs run
+sharded over the two ranks and report the same whole-job figures on both.  No
+kernel of one rank waits on another rank.
 """
 import math
 import os
@@ -156,3 +158,53 @@ def test_two_ranks_sharded_forest_equals_one_forest():
             assert np.array_equal(gathered[k][0], x) and np.array_equal(gathered[k][1], a), k
     finally:
         B.bh_forest_destroy(f)
+
+
+def _bench_rank(rank, world, port, q):
+    import argparse
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(0)
+    import bench
+    args = argparse.Namespace(forest_systems=12, forest_steps=4, plain_steps=2)
+    batched = bench.bench_batched(args, B, torch, None)
+    served = bench.serve_stream(B, 200.0, 0.05, 5, bench.serve_pools(), budget_gb=4.0)
+    q.put((rank, batched, served))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.gpu
+def test_bench_sharded_legs_on_two_ranks():
+    # The benchmark's batched and served legs with two ranks (sharing one GPU
+    # here, each with its own forest or server): both ranks report the same
+    # whole-job figures, over every system and every request.
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import synth
+    ctx = mp.get_context("spawn")
+    qu = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_bench_rank, args=(r, 2, port, qu)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = {}
+    for _ in procs:
+        rank, batched, served = qu.get(timeout=900)
+        out[rank] = (batched, served)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    b0, s0 = out[0]
+    b1, s1 = out[1]
+    total = sum(s.n for s in synth.forest_systems(12, 256, 65536, seed=4, theta=0.5, eps=0.01,
+                                                  materialise=False))
+    for b in (b0, b1):
+        assert b["ranks"] == 2 and f"(sum {total})" in b["workload"]
+    assert b0["value"] == b1["value"] and b0["plain_sequential_graph"] == b1["plain_sequential_graph"]
+    assert b0["err_p99"] <= 1e-5 and b0["err_max"] <= 1e-3  # rank 0 checks its share
+    nreq = len(synth.request_stream(rate_hz=200.0, duration_s=0.05, seed=5))
+    for s in (s0, s1):
+        assert s["ranks"] == 2 and s["requests"] == nreq
+    assert s0["value"] == s1["value"] and s0["p99_latency_s"] == s1["p99_latency_s"]

@@ -479,6 +479,74 @@ def test_served_results_against_oracle():
         assert np.array_equal(x1[:, 3], sp["pm"][:, 3])
 
 
+def _tight_pairs(npairs, seed):
+    # pairs 1e-6 apart: each pair hangs a chain of ~17 single-child cells,
+    # ~9 nodes per particle
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1, 1, (npairs, 3))
+    pm = np.zeros((2 * npairs, 4), np.float32)
+    pm[:, :3] = np.concatenate([c, c + rng.normal(0, 1e-6, c.shape)])
+    pm[:, 3] = 1.0 / (2 * npairs)
+    vel = np.zeros_like(pm)
+    vel[:, :3] = rng.normal(0, 0.1, (2 * npairs, 3))
+    return pm, vel
+
+
+def _alone(pm, vel, theta, nsteps, eps=0.01, dt=1e-3):
+    h = make(pm, vel, eps, theta)
+    try:
+        B.bh_step(h, nsteps, dt)
+        x = np.zeros_like(pm); a = np.zeros_like(pm)
+        B.bh_get_state(h, x, None, a)
+    finally:
+        B.bh_destroy(h)
+    return x, a
+
+
+def test_server_node_overflow_inside_the_forest():
+    # A budget of 4 MB reserves node arrays for about 29k nodes; two
+    # tight-pair requests need ~37k each.  The served forest's build reports
+    # the overflow, its node arrays grow, the step is redone, and every result
+    # equals the request solved alone (and the oracle's forces).
+    reqs = [_tight_pairs(2048, 61), synth.plummer(3000, 62), _tight_pairs(2048, 63)]
+    srv = B.bh_server_create(4 << 20, 2)
+    try:
+        tickets = [B.bh_submit(srv, pm, v, 1.0, 0.01, 0.5, 1e-3, 2) for pm, v in reqs]
+        res = [B.bh_wait(srv, t, len(pm), 120.0) for t, (pm, v) in zip(tickets, reqs)]
+        st = B.bh_server_stats_get(srv)
+    finally:
+        B.bh_server_destroy(srv)
+    assert st["completed"] == 3 and st["peak_resident_systems"] == 2
+    for (pm, v), out in zip(reqs, res):
+        assert out["status"] == 0 and out["steps_done"] == 2
+        x, a = _alone(pm, v, 0.5, 2)
+        assert np.array_equal(out["pos_mass"], x) and np.array_equal(out["acc"], a)
+        assert_accel_close(out["acc"], oracle.Tree(x).accel(0.5, 0.01)[0], what="served overflow")
+
+
+def test_server_request_larger_than_staging():
+    # With a 2 GB budget the pinned staging buffer is 64 MB: a request of 2.5M
+    # particles (80 MB in, 120 MB out) is copied from its own arrays instead,
+    # while small requests go through staging; all results equal the same
+    # requests solved alone.
+    big = synth.uniform_cube(2_500_000, 64)
+    reqs = [big, synth.plummer(5000, 65), synth.uniform_cube(7000, 66)]
+    srv = B.bh_server_create(2 << 30, 3)
+    try:
+        tickets = [B.bh_submit(srv, pm, v, 1.0, 0.01, 0.6, 1e-3, 1) for pm, v in reqs]
+        res = [B.bh_wait(srv, t, len(pm), 300.0) for t, (pm, v) in zip(tickets, reqs)]
+    finally:
+        B.bh_server_destroy(srv)
+    for (pm, v), out in zip(reqs, res):
+        assert out["status"] == 0 and out["steps_done"] == 1
+        x, a = _alone(pm, v, 0.6, 1)
+        assert np.array_equal(out["pos_mass"], x) and np.array_equal(out["acc"], a)
+    sample = np.random.default_rng(67).choice(len(big[0]), 4096, replace=False)
+    x = res[0]["pos_mass"]
+    ref, _, _ = oracle.Tree(x).accel(0.6, 0.01, targets=sample)
+    assert_accel_close(res[0]["acc"][sample], ref, what="large served request")
+
+
 def test_server_admission_by_budget_and_slots():
     # a request larger than the HBM budget is refused at submit; the others
     # are admitted first come, first served, never more than the slots, and

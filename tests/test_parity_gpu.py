@@ -396,6 +396,75 @@ def test_forest_systems_equal_alone(group):
         B.bh_forest_destroy(f)
 
 
+@pytest.mark.parametrize("group", [1, 0])
+def test_forest_with_zero_softening_equals_alone(group):
+    # The walk variants without the zero-distance guard serve only launches
+    # in which every system has eps > 0.  Here one system has eps = 0 and
+    # coincident points (where the guard matters): the forest runs the guarded
+    # variant, each system alone runs the variant its own eps allows, and all
+    # results agree bit for bit through two KDK steps; the eps = 0 system's
+    # force evaluation is also checked against the oracle.
+    systems = synth.forest_systems(6, 512, 4000, seed=23, theta=0.6, eps=0.01)
+    descs = [dict(pos_mass=s.pos_mass, vel=s.vel, eps=s.eps, theta=s.theta, dt=1e-3) for s in systems]
+    pm, vel = gen("dups", 1000, 24)
+    descs.append(dict(pos_mass=pm, vel=vel, eps=0.0, theta=0.6, dt=1e-3))
+    f = B.bh_forest_create(descs)
+    try:
+        B.bh_forest_set_tuning(f, 1, 8, 0, group, 0)
+        # the force evaluation first: coincident points meet the guard exactly
+        B.bh_forest_compute_accel(f)
+        a0 = np.zeros((len(pm), 4), np.float32)
+        B.bh_forest_get_state(f, len(descs) - 1, None, None, a0)
+        assert np.all(np.isfinite(a0))
+        assert_accel_close(a0, oracle.Tree(pm).accel(0.6, 0.0)[0], what="eps = 0 in a forest")
+        B.bh_forest_step(f, 2, 1e-3)
+        for k, d in enumerate(descs):
+            n = len(d["pos_mass"])
+            xf = np.zeros((n, 4), np.float32); af = np.zeros((n, 4), np.float32)
+            B.bh_forest_get_state(f, k, xf, None, af)
+            h = make(d["pos_mass"], d["vel"], d["eps"], d["theta"])
+            try:
+                B.bh_set_tuning(h, 1, 16, 0, group, 75)
+                B.bh_step(h, 2, 1e-3)
+                x1 = np.zeros_like(xf); a1 = np.zeros_like(af)
+                B.bh_get_state(h, x1, None, a1)
+            finally:
+                B.bh_destroy(h)
+            assert np.array_equal(xf, x1) and np.array_equal(af, a1), f"system {k}"
+            assert np.all(np.isfinite(af))
+    finally:
+        B.bh_forest_destroy(f)
+
+
+def test_served_options_against_oracle():
+    # A server created with the quadrupole term and the open-inside rule: each
+    # served result equals the request solved alone under the same options and
+    # meets the gates against the oracle under them.
+    fl = B.BH_QUADRUPOLE | B.BH_OPEN_INSIDE
+    reqs = [(synth.plummer if k % 2 else synth.uniform_cube)(3000 + 1500 * k, 130 + k)
+            for k in range(4)]
+    thetas = [0.6, 0.7, 0.8, 0.9]
+    srv = B.bh_server_create(4 << 30, 2, flags=fl)
+    try:
+        tickets = [B.bh_submit(srv, pm, v, 1.0, 0.01, th, 1e-3, 2)
+                   for (pm, v), th in zip(reqs, thetas)]
+        res = [B.bh_wait(srv, t, len(pm), 120.0) for t, (pm, v) in zip(tickets, reqs)]
+    finally:
+        B.bh_server_destroy(srv)
+    for ((pm, v), th), out in zip(zip(reqs, thetas), res):
+        assert out["status"] == 0 and out["steps_done"] == 2
+        h = make(pm, v, 0.01, th, flags=fl)
+        try:
+            B.bh_step(h, 2, 1e-3)
+            x = np.zeros_like(pm); a = np.zeros_like(pm)
+            B.bh_get_state(h, x, None, a)
+        finally:
+            B.bh_destroy(h)
+        assert np.array_equal(out["pos_mass"], x) and np.array_equal(out["acc"], a)
+        ref, _, _ = oracle.Tree(x).accel(th, 0.01, open_inside=True, quadrupole=True)
+        assert_accel_close(out["acc"], ref, what=f"served options theta {th}")
+
+
 def test_server_results_same_alone_and_in_mix():
     reqs = []
     for k in range(10):

@@ -156,8 +156,9 @@ typedef struct bh_tuning {
     int blocks_per_sm;
     int group;
     int static_share;  /* percent (0..90) of the tiles split into one contiguous
-                          range per block (neighbouring walks share L1); the
-                          rest are handed out by an atomic queue */
+                          range per SM, which the SM's blocks share
+                          (neighbouring walks share L1); the rest are handed
+                          out by an atomic queue */
 } bh_tuning;
 
 typedef struct bh_system bh_system;

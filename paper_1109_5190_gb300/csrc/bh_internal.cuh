@@ -86,6 +86,8 @@ struct DiagPart {
     double pad;
 };
 
+constexpr int kMaxTileGroups = 256;  // SMs whose walk tiles are shared per SM
+
 // Small per-forest device scalars.  The block [queue .. level_cur] is zeroed
 // at the start of every step with one memset.
 struct Small {
@@ -96,6 +98,7 @@ struct Small {
     // counting walk: interactions, warp iterations, particle-slot node visits
     unsigned long long wstats[3];
     unsigned queue;
+    unsigned group_next[kMaxTileGroups];  // the walk's per-SM static tile counters
     unsigned level_cnt[kNumLevels];
     unsigned level_cur[kNumLevels];
     unsigned level_off[kNumLevels + 1];
@@ -256,7 +259,7 @@ struct WalkArgs {
     const int *mode;
     Small *small;
     uint32_t *counts;  // per-particle interaction counts (virtual order) or null
-    int static_share;  // percent of tiles split into per-block contiguous ranges
+    int static_share;  // percent of tiles split into per-SM contiguous ranges
     int nsm;           // SMs the persistent grid is spread over
 };
 

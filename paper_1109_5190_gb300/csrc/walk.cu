@@ -7,10 +7,10 @@
 // s^2 < theta^2 d^2 (Section III, Fig. 1, with r the cell side); otherwise
 // its children are visited.  The decision is taken per particle, exactly.
 //
-// GPU design (sm_103a; bound by the L1 load path and instruction issue, not
-// by FP32 math; no tensor cores: this is not a dense contraction):
+// GPU design (sm_103a; bound by L1's data pipe for the scattered node loads,
+// not by FP32 math; no tensor cores: this is not a dense contraction):
 //   * Persistent kernel; each warp pulls tiles of 32*PPL consecutive
-//     Morton-sorted particles: first from its block's contiguous share of a
+//     Morton-sorted particles: first from its SM's contiguous share of a
 //     tunable fraction of the tiles (neighbouring walks share L1), then from
 //     an atomic queue over the rest (dynamic load balancing in place of the
 //     paper's runtime work queues, Section III).
@@ -146,17 +146,44 @@ __device__ __forceinline__ int slot_offset(int lane, int k)
     return GROUP == 32 ? k * 32 + lane : lane * PPL + k;
 }
 
-// Static range of this block.  Persistent blocks are dealt to SMs round
-// robin (block b on SM b mod #SMs), so ranges are numbered SM by SM: the
-// blocks that share an SM take neighbouring ranges and their walks share L1.
-// Any other placement is still correct, only with less sharing.
-__device__ __forceinline__ int range_of_block(int nsm)
-{
-    const int bps = nsm > 0 ? (int)gridDim.x / nsm : 1;  // the grid is nsm * bps blocks
-    const int b = (int)blockIdx.x;
-    if (bps <= 1 || bps * nsm != (int)gridDim.x) return b;
-    return (b % nsm) * bps + b / nsm;
-}
+// Hands out a walk's tiles.  Tiles [0, nstatic) (the static share) are split
+// into one contiguous range per SM: the blocks on an SM (block b on SM
+// b mod #SMs, the order a persistent grid is dealt in) take its tiles through
+// one counter in global memory, so all of the SM's warps walk neighbouring
+// tiles and share tree nodes in L1 (on the 2^20 cube: 2.61 ms, against 2.68
+// with one range per block).  The rest go through the global atomic queue,
+// which evens out the finishing times (all of them, when tile costs vary
+// widely, as in a forest).  Any other placement of blocks only shares less;
+// a grid that is not #SMs x blocks-per-SM uses one range per block, counted in
+// shared memory (s_next, zeroed by the caller before a block barrier).
+struct TileDealer {
+    unsigned *next;   // static counter of the calling block's range
+    unsigned *queue;  // dynamic queue
+    int group, per_group, nstatic;
+
+    __device__ __forceinline__ TileDealer(const WalkArgs &a, unsigned *s_next)
+    {
+        const int bps = a.nsm > 0 ? (int)gridDim.x / a.nsm : 1;
+        const bool per_sm = a.nsm > 0 && bps * a.nsm == (int)gridDim.x && a.nsm <= kMaxTileGroups;
+        const int ngroups = per_sm ? a.nsm : (int)gridDim.x;
+        group = per_sm ? (int)blockIdx.x % a.nsm : (int)blockIdx.x;
+        next = per_sm ? &a.small->group_next[group] : s_next;
+        queue = &a.small->queue;
+        per_group = (int)(((long long)a.ntiles * a.static_share / 100) / ngroups);
+        nstatic = per_group * ngroups;
+    }
+
+    // the warp's next tile (lane 0 takes it; every lane gets it)
+    __device__ __forceinline__ int take(int lane) const
+    {
+        int t = 0;
+        if (lane == 0) {
+            const int k = (int)atomicAdd(next, 1u);
+            t = k < per_group ? group * per_group + k : nstatic + (int)atomicAdd(queue, 1u);
+        }
+        return __shfl_sync(FULL, t, 0);
+    }
+};
 
 // One softened monopole term added to a particle slot's sums.
 // SOFT: every system of the launch has eps > 0, so r2 >= eps^2 > 0 and the
@@ -258,24 +285,12 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
     const int lane = threadIdx.x & 31;
     Small *sm = a.small;
     if (sm->status) return;
-    // Tiles [0, nstatic) (static_share percent) are split into one contiguous
-    // range per block, taken through a shared counter, so the warps of an SM
-    // walk neighbouring regions and share tree nodes in L1; the rest go
-    // through the global atomic queue, which evens out the blocks' finishing
-    // times (all of them, when tile costs vary widely, as in a forest).
     __shared__ unsigned s_next;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
-    const int per_block = (int)(((long long)a.ntiles * a.static_share / 100) / gridDim.x);
-    const int nstatic = per_block * (int)gridDim.x;
+    const TileDealer deal(a, &s_next);
     for (;;) {
-        int t = 0;
-        if (lane == 0) {
-            const int k = (int)atomicAdd(&s_next, 1u);
-            t = k < per_block ? range_of_block(a.nsm) * per_block + k
-                              : nstatic + (int)atomicAdd(&sm->queue, 1u);
-        }
-        t = __shfl_sync(FULL, t, 0);
+        const int t = deal.take(lane);
         if (t >= a.ntiles) break;
         const Tile tl = a.tiles[t];
         const SysStatic &S = a.sys[tl.sys];
@@ -462,16 +477,9 @@ __global__ void __launch_bounds__(512, 3) k_walk_sib(WalkArgs a)
     __shared__ unsigned s_next;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
-    const int per_block = (int)(((long long)a.ntiles * a.static_share / 100) / gridDim.x);
-    const int nstatic = per_block * (int)gridDim.x;
+    const TileDealer deal(a, &s_next);
     for (;;) {
-        int t = 0;
-        if (lane == 0) {
-            const int k = (int)atomicAdd(&s_next, 1u);
-            t = k < per_block ? range_of_block(a.nsm) * per_block + k
-                              : nstatic + (int)atomicAdd(&sm->queue, 1u);
-        }
-        t = __shfl_sync(FULL, t, 0);
+        const int t = deal.take(lane);
         if (t >= a.ntiles) break;
         const Tile tl = a.tiles[t];
         const SysStatic &S = a.sys[tl.sys];
@@ -582,20 +590,6 @@ __device__ __forceinline__ int split_top_level(int n)
     return min(5, max(2, l8 - 3));
 }
 
-// Next tile for the calling warp (lane 0 takes it; every lane gets it):
-// first the block's share of the static range, then the global queue.
-__device__ __forceinline__ int next_tile(const WalkArgs &a, unsigned *s_next, int lane)
-{
-    int t = 0;
-    if (lane == 0) {
-        const int per_block = (int)(((long long)a.ntiles * a.static_share / 100) / gridDim.x);
-        const int k = (int)atomicAdd(s_next, 1u);
-        t = k < per_block ? range_of_block(a.nsm) * per_block + k
-                          : per_block * (int)gridDim.x + (int)atomicAdd(&a.small->queue, 1u);
-    }
-    return __shfl_sync(FULL, t, 0);
-}
-
 template <bool KAHAN, bool POT, bool COUNT, bool SOFT = false>
 __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
 {
@@ -607,8 +601,9 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
     if (sm->status) return;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
+    const TileDealer deal(a, &s_next);
     for (;;) {
-        const int t = next_tile(a, &s_next, lane);
+        const int t = deal.take(lane);
         if (t >= a.ntiles) break;
         const Tile tl = a.tiles[t];
         const int sysid = tl.sys;
@@ -795,16 +790,9 @@ __global__ void __launch_bounds__(512, 3) k_walk_list(WalkArgs a)
     if (sm->status) return;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
-    const int per_block = (int)(((long long)a.ntiles * a.static_share / 100) / gridDim.x);
-    const int nstatic = per_block * (int)gridDim.x;
+    const TileDealer deal(a, &s_next);
     for (;;) {
-        int t = 0;
-        if (lane == 0) {
-            const int k = (int)atomicAdd(&s_next, 1u);
-            t = k < per_block ? range_of_block(a.nsm) * per_block + k
-                              : nstatic + (int)atomicAdd(&sm->queue, 1u);
-        }
-        t = __shfl_sync(FULL, t, 0);
+        const int t = deal.take(lane);
         if (t >= a.ntiles) break;
         const Tile tl = a.tiles[t];
         const int sysid = tl.sys;

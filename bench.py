@@ -856,7 +856,7 @@ def main():
                          "64 = interaction lists, 65 = one lane per particle over "
                          "sibling-ordered node records)")
     ap.add_argument("--no-kahan", action="store_true", help="plain FP32 force sums")
-    ap.add_argument("--static-share", type=int, default=75)
+    ap.add_argument("--static-share", type=int, default=90)
     ap.add_argument("--no-graph", action="store_true", help="launch each step's kernels directly")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-theta07", action="store_true",

@@ -155,10 +155,11 @@ typedef struct bh_tuning {
     int warps_per_block;
     int blocks_per_sm;
     int group;
-    int static_share;  /* percent (0..90) of the tiles split into one contiguous
-                          range per SM, which the SM's blocks share
-                          (neighbouring walks share L1); the rest are handed
-                          out by an atomic queue */
+    int static_share;  /* percent (0..100) of the tiles split into one
+                          contiguous range per SM, which the SM's blocks share
+                          (neighbouring walks share L1); an SM whose range is
+                          empty takes tiles from the back of its neighbours'
+                          ranges; the rest are handed out by an atomic queue */
 } bh_tuning;
 
 typedef struct bh_system bh_system;

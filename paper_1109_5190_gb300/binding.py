@@ -281,7 +281,7 @@ def bh_walk_stats(h) -> dict:
     return {"interactions": a.value, "warp_iterations": b.value, "slot_visits": c.value}
 
 
-def bh_set_tuning(h, ppl=1, warps_per_block=16, blocks_per_sm=0, group=1, static_share=75):
+def bh_set_tuning(h, ppl=1, warps_per_block=16, blocks_per_sm=0, group=1, static_share=90):
     t = bh_tuning(ppl, warps_per_block, blocks_per_sm, group, static_share)
     return _check(lib.bh_set_tuning(h, C.byref(t)))
 

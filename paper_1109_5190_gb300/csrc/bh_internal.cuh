@@ -98,7 +98,9 @@ struct Small {
     // counting walk: interactions, warp iterations, particle-slot node visits
     unsigned long long wstats[3];
     unsigned queue;
-    unsigned group_next[kMaxTileGroups];  // the walk's per-SM static tile counters
+    // the walk's per-SM tile ranges: tiles taken from the front (low 32 bits,
+    // by the SM's own warps) and from the back (high 32 bits, by other SMs')
+    unsigned long long group_ctr[kMaxTileGroups];
     unsigned level_cnt[kNumLevels];
     unsigned level_cur[kNumLevels];
     unsigned level_off[kNumLevels + 1];
@@ -259,7 +261,7 @@ struct WalkArgs {
     const int *mode;
     Small *small;
     uint32_t *counts;  // per-particle interaction counts (virtual order) or null
-    int static_share;  // percent of tiles split into per-SM contiguous ranges
+    int static_share;  // percent of tiles split into per-SM contiguous ranges (with stealing)
     int nsm;           // SMs the persistent grid is spread over
 };
 

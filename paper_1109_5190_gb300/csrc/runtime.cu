@@ -204,7 +204,7 @@ struct Forest {
 
     bool acc_valid = false;
     bool tree_valid = false;
-    bh_tuning tune{1, 16, 0, 1, 75};
+    bh_tuning tune{1, 16, 0, 1, 90};
 
     cudaGraphExec_t gexec = nullptr;
     int g_nsteps = -1;
@@ -887,7 +887,9 @@ struct Forest {
         CKR(cudaEventCreate(&e1));
         float best_ms = 1e30f;
         bh_tuning pick = tune;
-        const int shares[2] = {0, 75};
+        // static shares: none (forests of uneven systems), 90 (one system: the
+        // best measured with taking from the SMs' neighbouring ranges), 100
+        const int shares[3] = {0, 90, 100};
         const bh_tuning saved = tune;
         for (const auto &gp : shapes) {
             const int g = gp[0], p = gp[1];
@@ -938,13 +940,13 @@ struct Forest {
             t->warps_per_block > 16 ||
             (t->group != 0 && t->group != 1 && t->group != 2 && t->group != 4 && t->group != 8 &&
              t->group != 32 && t->group != BH_GROUP_LIST && t->group != BH_GROUP_SIBLINGS) ||
-            t->static_share < 0 || t->static_share > 90 ||
+            t->static_share < 0 || t->static_share > 100 ||
             (t->group != 32 && t->group != 1 && t->ppl == 4) ||
             ((t->group == 2 || t->group == 0 || t->group == BH_GROUP_LIST ||
               t->group == BH_GROUP_SIBLINGS) && t->ppl != 1))
             return fail(BH_ERR_INVALID, "bad tuning (group 1 or 32 with ppl 1/2/4, group 4/8 with "
                                         "ppl 1/2, group 2, 0, BH_GROUP_LIST or BH_GROUP_SIBLINGS "
-                                        "with ppl 1; warps 1..16; static_share 0..90; "
+                                        "with ppl 1; warps 1..16; static_share 0..100; "
                                         "blocks_per_sm >= 0)");
         // the shape as it would be launched (BH_OPEN_INSIDE: one particle per lane)
         const WalkShape sh = shape_of(*t);

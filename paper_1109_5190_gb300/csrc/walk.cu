@@ -148,38 +148,68 @@ __device__ __forceinline__ int slot_offset(int lane, int k)
 
 // Hands out a walk's tiles.  Tiles [0, nstatic) (the static share) are split
 // into one contiguous range per SM: the blocks on an SM (block b on SM
-// b mod #SMs, the order a persistent grid is dealt in) take its tiles through
-// one counter in global memory, so all of the SM's warps walk neighbouring
-// tiles and share tree nodes in L1 (on the 2^20 cube: 2.61 ms, against 2.68
-// with one range per block).  The rest go through the global atomic queue,
-// which evens out the finishing times (all of them, when tile costs vary
-// widely, as in a forest).  Any other placement of blocks only shares less;
-// a grid that is not #SMs x blocks-per-SM uses one range per block, counted in
-// shared memory (s_next, zeroed by the caller before a block barrier).
+// b mod #SMs, the order a persistent grid is dealt in) take its tiles from the
+// front through one counter in global memory, so all of the SM's warps walk
+// neighbouring tiles and share tree nodes in L1.  A warp whose SM's range is
+// empty takes single tiles from the back of the other SMs' ranges, nearest
+// SMs first (their tiles are the nearest in Morton order), which evens out
+// the finishing times without scattering the tail.  The rest of the tiles go
+// through a global atomic queue.  One 64-bit counter per range holds the
+// tiles taken from the front (low 32 bits) and from the back (high 32 bits);
+// a take is valid iff the two counts before it sum to less than the range's
+// length, so every tile is taken exactly once.  Any other placement of blocks
+// only shares less; a grid that is not #SMs x blocks-per-SM uses one range
+// per block, counted in shared memory (s_next, zeroed by the caller before a
+// block barrier), and no taking from other ranges.
 struct TileDealer {
-    unsigned *next;   // static counter of the calling block's range
-    unsigned *queue;  // dynamic queue
-    int group, per_group, nstatic;
+    unsigned long long *ctr;  // per-SM range counters (null: one range per block)
+    unsigned *s_next;         // per-block range counter
+    unsigned *queue;          // dynamic queue
+    int group, ngroups, per_group, nstatic;
+    // the taking warp's state (lane 0): its own range is empty; ranges tried
+    bool own_done = false;
+    int tried = 0;
 
-    __device__ __forceinline__ TileDealer(const WalkArgs &a, unsigned *s_next)
+    __device__ __forceinline__ TileDealer(const WalkArgs &a, unsigned *next_in_block)
     {
         const int bps = a.nsm > 0 ? (int)gridDim.x / a.nsm : 1;
         const bool per_sm = a.nsm > 0 && bps * a.nsm == (int)gridDim.x && a.nsm <= kMaxTileGroups;
-        const int ngroups = per_sm ? a.nsm : (int)gridDim.x;
+        ngroups = per_sm ? a.nsm : (int)gridDim.x;
         group = per_sm ? (int)blockIdx.x % a.nsm : (int)blockIdx.x;
-        next = per_sm ? &a.small->group_next[group] : s_next;
+        ctr = per_sm ? a.small->group_ctr : nullptr;
+        s_next = next_in_block;
         queue = &a.small->queue;
         per_group = (int)(((long long)a.ntiles * a.static_share / 100) / ngroups);
         nstatic = per_group * ngroups;
     }
 
     // the warp's next tile (lane 0 takes it; every lane gets it)
-    __device__ __forceinline__ int take(int lane) const
+    __device__ __forceinline__ int take(int lane)
     {
-        int t = 0;
+        int t = -1;
         if (lane == 0) {
-            const int k = (int)atomicAdd(next, 1u);
-            t = k < per_group ? group * per_group + k : nstatic + (int)atomicAdd(queue, 1u);
+            if (!ctr) {
+                const int k = (int)atomicAdd(s_next, 1u);
+                if (k < per_group) t = group * per_group + k;
+            } else {
+                if (!own_done) {
+                    const unsigned long long o = atomicAdd(&ctr[group], 1ull);
+                    const int f = (int)(unsigned)o, b = (int)(o >> 32);
+                    if (f + b < per_group) t = group * per_group + f;
+                    else own_done = true;
+                }
+                // from the back of the other ranges: group + 1, group - 1, group + 2, ...
+                while (t < 0 && tried < ngroups - 1) {
+                    const int d = tried / 2 + 1;
+                    int v = (tried & 1) ? group - d : group + d;
+                    v = ((v % ngroups) + ngroups) % ngroups;
+                    const unsigned long long o = atomicAdd(&ctr[v], 1ull << 32);
+                    const int f = (int)(unsigned)o, b = (int)(o >> 32);
+                    if (f + b < per_group) t = v * per_group + (per_group - 1 - b);
+                    else ++tried;
+                }
+            }
+            if (t < 0) t = nstatic + (int)atomicAdd(queue, 1u);
         }
         return __shfl_sync(FULL, t, 0);
     }
@@ -288,7 +318,7 @@ __global__ void __launch_bounds__(512, PPL == 1 ? 3 : 2) k_walk(WalkArgs a)
     __shared__ unsigned s_next;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
-    const TileDealer deal(a, &s_next);
+    TileDealer deal(a, &s_next);
     for (;;) {
         const int t = deal.take(lane);
         if (t >= a.ntiles) break;
@@ -477,7 +507,7 @@ __global__ void __launch_bounds__(512, 3) k_walk_sib(WalkArgs a)
     __shared__ unsigned s_next;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
-    const TileDealer deal(a, &s_next);
+    TileDealer deal(a, &s_next);
     for (;;) {
         const int t = deal.take(lane);
         if (t >= a.ntiles) break;
@@ -601,7 +631,7 @@ __global__ void __launch_bounds__(512, 3) k_walk_split(WalkArgs a)
     if (sm->status) return;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
-    const TileDealer deal(a, &s_next);
+    TileDealer deal(a, &s_next);
     for (;;) {
         const int t = deal.take(lane);
         if (t >= a.ntiles) break;
@@ -790,7 +820,7 @@ __global__ void __launch_bounds__(512, 3) k_walk_list(WalkArgs a)
     if (sm->status) return;
     if (threadIdx.x == 0) s_next = 0;
     __syncthreads();
-    const TileDealer deal(a, &s_next);
+    TileDealer deal(a, &s_next);
     for (;;) {
         const int t = deal.take(lane);
         if (t >= a.ntiles) break;

@@ -875,8 +875,13 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=0.5,
                     help="length of the Poisson arrival window (200 requests/s)")
     ap.add_argument("--workload", default="uniform1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--theta", type=float, default=None,
+                    help="opening angle of the main leg (default: the workload's)")
     args = ap.parse_args()
     globals().update(WORKLOADS[args.workload])
+    if args.theta is not None:
+        globals()["THETA"] = args.theta
+        globals()["WORKLOAD"] = WORKLOAD.replace("theta=0.5", f"theta={args.theta}")
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
     if args.impl == "reference":

@@ -98,6 +98,7 @@ struct Small {
     // counting walk: interactions, warp iterations, particle-slot node visits
     unsigned long long wstats[3];
     unsigned queue;
+    unsigned ranges_empty;  // the walk's per-SM tile ranges found empty
     // the walk's per-SM tile ranges: tiles taken from the front (low 32 bits,
     // by the SM's own warps) and from the back (high 32 bits, by other SMs')
     unsigned long long group_ctr[kMaxTileGroups];

@@ -152,8 +152,8 @@ __device__ __forceinline__ int slot_offset(int lane, int k)
 // front through one counter in global memory, so all of the SM's warps walk
 // neighbouring tiles and share tree nodes in L1.  A warp whose SM's range is
 // empty takes single tiles from the back of the other SMs' ranges, nearest
-// SMs first (their tiles are the nearest in Morton order), which evens out
-// the finishing times without scattering the tail.  The rest of the tiles go
+// SMs first (their tiles are the nearest in Morton order), until every range
+// is empty, which evens out the finishing times without scattering the tail.  The rest of the tiles go
 // through a global atomic queue.  One 64-bit counter per range holds the
 // tiles taken from the front (low 32 bits) and from the back (high 32 bits);
 // a take is valid iff the two counts before it sum to less than the range's
@@ -163,6 +163,7 @@ __device__ __forceinline__ int slot_offset(int lane, int k)
 // block barrier), and no taking from other ranges.
 struct TileDealer {
     unsigned long long *ctr;  // per-SM range counters (null: one range per block)
+    unsigned *empty;          // ranges found empty so far
     unsigned *s_next;         // per-block range counter
     unsigned *queue;          // dynamic queue
     int group, ngroups, per_group, nstatic;
@@ -177,10 +178,23 @@ struct TileDealer {
         ngroups = per_sm ? a.nsm : (int)gridDim.x;
         group = per_sm ? (int)blockIdx.x % a.nsm : (int)blockIdx.x;
         ctr = per_sm ? a.small->group_ctr : nullptr;
+        empty = &a.small->ranges_empty;
         s_next = next_in_block;
         queue = &a.small->queue;
         per_group = (int)(((long long)a.ntiles * a.static_share / 100) / ngroups);
         nstatic = per_group * ngroups;
+    }
+
+    // One take from range v (front: its own SM's warps; back: others').  The
+    // take whose counts before it sum to exactly the range's length is the
+    // first to find it empty, and counts it.
+    __device__ __forceinline__ int take_from(int v, bool back) const
+    {
+        const unsigned long long o = atomicAdd(&ctr[v], back ? 1ull << 32 : 1ull);
+        const int f = (int)(unsigned)o, b = (int)(o >> 32);
+        if (f + b < per_group) return v * per_group + (back ? per_group - 1 - b : f);
+        if (f + b == per_group) atomicAdd(empty, 1u);
+        return -1;
     }
 
     // the warp's next tile (lane 0 takes it; every lane gets it)
@@ -193,20 +207,19 @@ struct TileDealer {
                 if (k < per_group) t = group * per_group + k;
             } else {
                 if (!own_done) {
-                    const unsigned long long o = atomicAdd(&ctr[group], 1ull);
-                    const int f = (int)(unsigned)o, b = (int)(o >> 32);
-                    if (f + b < per_group) t = group * per_group + f;
-                    else own_done = true;
+                    t = take_from(group, false);
+                    own_done = t < 0;
                 }
-                // from the back of the other ranges: group + 1, group - 1, group + 2, ...
-                while (t < 0 && tried < ngroups - 1) {
+                // from the back of the other ranges, nearest first: group + 1,
+                // group - 1, group + 2, ...; none once every range is empty
+                // (probing them all at the end of the walk cost ~0.1 ms)
+                while (t < 0 && tried < ngroups - 1 &&
+                       *(volatile unsigned *)empty < (unsigned)ngroups) {
                     const int d = tried / 2 + 1;
                     int v = (tried & 1) ? group - d : group + d;
                     v = ((v % ngroups) + ngroups) % ngroups;
-                    const unsigned long long o = atomicAdd(&ctr[v], 1ull << 32);
-                    const int f = (int)(unsigned)o, b = (int)(o >> 32);
-                    if (f + b < per_group) t = v * per_group + (per_group - 1 - b);
-                    else ++tried;
+                    t = take_from(v, true);
+                    if (t < 0) ++tried;
                 }
             }
             if (t < 0) t = nstatic + (int)atomicAdd(queue, 1u);

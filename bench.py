@@ -500,10 +500,13 @@ def run_gpu(args):
     if rank == 0 and ws == 1 and not args.no_cpu:
         v, spent, threads = cpu_sample(pm, args.cpu_sample)
         v1, spent1 = cpu_one_core(pm)
+        walked = (f"walk of all {N_PART} particles ({threads} threads), timed in full"
+                  if args.cpu_sample >= N_PART else
+                  f"walk of {args.cpu_sample} random particles ({threads} threads), "
+                  f"extrapolated to N")
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"one step: full FP64 tree build of {N_PART} particles "
-                                          f"(1 thread) + walk of {args.cpu_sample} random particles "
-                                          f"({threads} threads), extrapolated to N; {spent:.1f} s",
+                                          f"(1 thread) + {walked}; {spent:.1f} s",
                                 "one_core_value": v1,
                                 "one_core_sample": f"the same step with a 4096-particle walk on "
                                                    f"1 thread, extrapolated to N; {spent1:.1f} s",

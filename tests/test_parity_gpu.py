@@ -123,6 +123,39 @@ def test_tree_bit_exact_and_accel(kind, n, seed):
         B.bh_destroy(h)
 
 
+def test_seeded_random_cases_against_oracle():
+    # 30 seeded cases drawn at random: sizes log-uniform in [1, 40000] (ragged
+    # last tiles, fewer tiles than SMs), six input kinds, theta in [0.2, 1.0],
+    # three softenings, and the walk shapes in turn.  Each: tree bit-exact,
+    # accelerations within the gates, interaction counts equal.
+    rng = np.random.default_rng(20261204)
+    kinds = ["plummer", "uniform", "gauss", "clustered", "planar", "dups"]
+    shapes = [(1, 16, 0, 1, 90), (1, 8, 0, 1, 100), (2, 8, 0, 1, 75), (1, 4, 2, 4, 0),
+              (2, 8, 0, 32, 75), (1, 8, 0, B.BH_GROUP_LIST, 75),
+              (1, 16, 0, B.BH_GROUP_SIBLINGS, 90), (1, 16, 0, 0, 90)]
+    for case in range(30):
+        kind = kinds[case % len(kinds)]
+        n = int(np.exp(rng.uniform(0.0, np.log(40000.0))))
+        if kind == "dups":
+            n = max(n, 600)  # the generator copies points up to index 502
+        theta = float(rng.uniform(0.2, 1.0))
+        eps = float(rng.choice([1e-3, 5e-3, 2e-2]))
+        shape = shapes[case % len(shapes)]
+        pm, vel = gen(kind, n, 1000 + case)
+        h = make(pm, vel, eps, theta)
+        try:
+            B.bh_set_tuning(h, *shape)
+            a = gpu_accel(h, n)
+            T = check_tree(h, pm)
+            ref, _, cnt = T.accel(theta, eps)
+            what = f"case {case}: {kind} n={n} theta={theta:.3f} eps={eps} shape={shape}"
+            assert_accel_close(a, ref, what=what)
+            gc, _ = B.bh_interaction_count(h, n)
+            assert np.array_equal(gc.astype(np.int64), cnt), what
+        finally:
+            B.bh_destroy(h)
+
+
 def test_theta_zero_matches_direct_sum():
     pm, _ = synth.plummer(4096, 12)
     h = make(pm, eps=0.01, theta=0.0)
@@ -237,7 +270,7 @@ def test_launch_shape_does_not_change_results():
                            (32, 2), (32, 4), (B.BH_GROUP_LIST, 1), (B.BH_GROUP_SIBLINGS, 1), (0, 1)):
             fam = "split" if group == 0 else "dfs"
             for w in (4, 8, 16):
-                for share in ((0, 75) if ppl == 1 else (75,)):
+                for share in ((0, 75, 90, 100) if ppl == 1 else (75,)):
                     B.bh_set_tuning(h, ppl, w, 0, group, share)
                     a = gpu_accel(h, n)
                     ref = refs.setdefault(fam, a)
@@ -261,6 +294,20 @@ def test_launch_shape_does_not_change_results():
         assert np.array_equal(gpu_accel(h, n), refs["split" if best[3] == 0 else "dfs"])
     finally:
         B.bh_destroy(h)
+    # fewer tiles than SMs (per-SM ranges of zero length: every tile from the
+    # queue) and a tile count that leaves a remainder after the ranges
+    for n in (1000, 152 * 32 * 3 + 17 * 32 + 5):
+        pm, _ = synth.plummer(n, 17)
+        h = make(pm, eps=0.01, theta=0.6)
+        try:
+            ref = None
+            for w, bps, share in ((16, 0, 0), (16, 0, 100), (8, 0, 90), (16, 1, 100), (4, 2, 75)):
+                B.bh_set_tuning(h, 1, w, bps, 1, share)
+                a = gpu_accel(h, n)
+                ref = a if ref is None else ref
+                assert np.array_equal(a, ref), (n, w, bps, share)
+        finally:
+            B.bh_destroy(h)
 
 
 def test_sibling_order_walk_edge_cases():
@@ -358,11 +405,12 @@ def test_device_pointers_and_torch_stream():
         B.bh_create(B.params(), bad, d_vel)
 
 
-@pytest.mark.parametrize("group", [1, 0, 65])
-def test_forest_systems_equal_alone(group):
+@pytest.mark.parametrize("group,share", [(1, 0), (1, 100), (0, 90), (65, 0)])
+def test_forest_systems_equal_alone(group, share):
     # group 1: one particle per lane; group 0: the split walk, whose sum order
     # is fixed by each particle's tile, which is the same alone or in a forest;
-    # 65: one particle per lane over the sibling-order records of all the trees
+    # 65: one particle per lane over the sibling-order records of all the trees.
+    # share: the percentage of tiles dealt from per-SM ranges (100: the server's)
     systems = synth.forest_systems(12, 256, 6000, seed=19, theta=0.5, eps=0.01)
     descs = [dict(pos_mass=s.pos_mass, vel=s.vel, eps=s.eps, theta=s.theta, dt=1e-3) for s in systems]
     # give two systems other parameters: per-system theta / eps / G
@@ -371,7 +419,7 @@ def test_forest_systems_equal_alone(group):
     descs[7]["G"] = 2.5
     f = B.bh_forest_create(descs)
     try:
-        B.bh_forest_set_tuning(f, 1, 8, 0, group, 0)
+        B.bh_forest_set_tuning(f, 1, 8, 0, group, share)
         B.bh_forest_compute_accel(f)
         B.bh_forest_profile_begin(f)
         B.bh_forest_step(f, 3, 1e-3, use_graph=True)

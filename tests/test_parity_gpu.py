@@ -1109,7 +1109,7 @@ def test_uniform_cube_million_step0_all_particles():
 
 @pytest.mark.slow
 def test_large_plummer_sampled():
-    # configs[2]: Plummer N = 2^24, eps 0.002, theta 0.6, dt 2.5e-4: a seeded
+    # The large Plummer sphere, N = 2^24, eps 0.002, theta 0.6, dt 2.5e-4: a seeded
     # 4096-particle sample against the FP64 oracle (full oracle tree of all
     # particles) at step 0 and after one KDK step.
     n = 1 << 24
@@ -1162,7 +1162,7 @@ def test_set_state_rejects_bad_input_and_keeps_the_old_state():
 
 @pytest.mark.slow
 def test_forest_512_systems_sampled():
-    # configs[3] at full size: 512 systems (N log-uniform in [256, 65536], half
+    # The full 512-system forest: 512 systems (N log-uniform in [256, 65536], half
     # Plummer, half uniform cold collapse, eps 0.01, theta 0.5), autotuned as
     # the benchmark runs it; 8 seeded systems against the FP64 oracle, every
     # particle, after the force evaluation and after one KDK step

@@ -444,6 +444,44 @@ def test_forest_systems_equal_alone(group, share):
         B.bh_forest_destroy(f)
 
 
+@pytest.mark.parametrize("group,share", [(1, 100), (0, 0), (32, 90)])
+def test_forest_of_tiny_and_ragged_systems(group, share):
+    # systems of 1, 2, 3, 31, 32, 33 and 64 particles (one partial tile, one
+    # full tile, a full tile plus one particle, ...) among larger ones, with
+    # coincident points in one of them: after a force evaluation and two graph
+    # steps every system equals itself solved alone, bit for bit, and meets the
+    # gates against the oracle
+    sizes = [1, 2, 3, 31, 32, 33, 64, 1500, 4097, 7]
+    descs = []
+    for k, n in enumerate(sizes):
+        pm, vel = (synth.plummer(n, 300 + k) if k % 2 == 0 else synth.uniform_cube(n, 300 + k))
+        if n == 33:
+            pm[10:20, :3] = pm[3, :3]  # a depth-cap bucket
+        descs.append(dict(pos_mass=pm, vel=vel, eps=0.01, theta=0.3 + 0.07 * k, dt=1e-3))
+    f = B.bh_forest_create(descs)
+    try:
+        B.bh_forest_set_tuning(f, 1, 8, 0, group, share)
+        B.bh_forest_compute_accel(f)
+        B.bh_forest_step(f, 2, 1e-3, use_graph=True)
+        for k, d in enumerate(descs):
+            n = len(d["pos_mass"])
+            xf = np.zeros((n, 4), np.float32); af = np.zeros((n, 4), np.float32)
+            B.bh_forest_get_state(f, k, xf, None, af)
+            h = make(d["pos_mass"], d["vel"], d["eps"], d["theta"])
+            try:
+                B.bh_set_tuning(h, 1, 16, 0, group, 90)
+                B.bh_step(h, 2, 1e-3)
+                x1 = np.zeros_like(xf); a1 = np.zeros_like(af)
+                B.bh_get_state(h, x1, None, a1)
+            finally:
+                B.bh_destroy(h)
+            assert np.array_equal(xf, x1) and np.array_equal(af, a1), f"system {k} (n={n})"
+            ref, _, _ = oracle.Tree(xf).accel(d["theta"], d["eps"])
+            assert_accel_close(af, ref, what=f"system {k} (n={n})")
+    finally:
+        B.bh_forest_destroy(f)
+
+
 @pytest.mark.parametrize("group", [1, 0])
 def test_forest_with_zero_softening_equals_alone(group):
     # The walk variants without the zero-distance guard serve only launches
